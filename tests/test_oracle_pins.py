@@ -1,0 +1,420 @@
+"""Pins of the CPU oracle against facts fixed outside the oracle itself.
+
+Each test checks the oracle against a closed form, an exact invariant of the
+scheme, brute force on a tiny mesh, a value printed in the paper, or a
+convergence rate -- never against a retyped copy of its own formula.
+"""
+from fractions import Fraction
+from math import sqrt
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle.dg_elastic import ElasticDG, A_of, abs_A, weighted_trace, hdg_flux
+import workloads as wl
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- GLL, D, SBP
+@pytest.mark.parametrize("N,nodes,weights", [
+    (1, [-1, 1], [1, 1]),
+    (2, [-1, 0, 1], [1 / 3, 4 / 3, 1 / 3]),
+    (3, [-1, -1 / sqrt(5), 1 / sqrt(5), 1], [1 / 6, 5 / 6, 5 / 6, 1 / 6]),
+    (4, [-1, -sqrt(3 / 7), 0, sqrt(3 / 7), 1], [1 / 10, 49 / 90, 32 / 45, 49 / 90, 1 / 10]),
+])
+def test_gll_closed_forms(N, nodes, weights):
+    r, w = oracle.gll(N)
+    np.testing.assert_allclose(r, nodes, atol=1e-15)
+    np.testing.assert_allclose(w, weights, atol=1e-15)
+
+
+@pytest.mark.parametrize("N", range(1, 9))
+def test_gll_quadrature_degree(N):
+    r, w = oracle.gll(N)
+    for q in range(2 * N):
+        exact = 0.0 if q % 2 else 2.0 / (q + 1)
+        assert abs(np.sum(w * r ** q) - exact) < 1e-13
+    # GLL is not exact at degree 2N (a discriminating check of the rule)
+    assert abs(np.sum(w * r ** (2 * N)) - 2.0 / (2 * N + 1)) > 1e-6
+
+
+@pytest.mark.parametrize("N", range(1, 9))
+def test_derivative_matrix_exact_and_sbp(N):
+    r, w = oracle.gll(N)
+    D = oracle.lagrange_derivative_matrix(r)
+    for q in range(N + 1):
+        d_exact = q * r ** (q - 1) if q > 0 else np.zeros_like(r)
+        np.testing.assert_allclose(D @ r ** q, d_exact, atol=1e-11)
+    W = np.diag(w)
+    Bnd = np.zeros((N + 1, N + 1))
+    Bnd[0, 0], Bnd[-1, -1] = -1.0, 1.0
+    np.testing.assert_allclose(W @ D + D.T @ W, Bnd, atol=1e-13)
+
+
+# ------------------------------------------------------------ system and |A|
+def test_A_is_elastodynamics():
+    """A(n) u = -(sigma n, Voigt(sym(n (x) v))) for a random state and normal."""
+    rng = np.random.default_rng(0)
+    n = rng.standard_normal(3)
+    v = rng.standard_normal(3)
+    S = rng.standard_normal((3, 3))
+    S = S + S.T
+    s_voigt = np.array([S[0, 0], S[1, 1], S[2, 2], S[1, 2], S[0, 2], S[0, 1]])
+    out = A_of(n) @ np.concatenate([v, s_voigt])
+    np.testing.assert_allclose(out[:3], -S @ n, atol=1e-14)
+    E = 0.5 * (np.outer(n, v) + np.outer(v, n))
+    np.testing.assert_allclose(out[3:], -np.array([E[0, 0], E[1, 1], E[2, 2],
+                                                   2 * E[1, 2], 2 * E[0, 2], 2 * E[0, 1]]), atol=1e-14)
+
+
+def test_absA_axis_normal_by_hand():
+    """n = e1: B^T B = I, so |A| = diag(I_3, B B^T) = diag(1,1,1, 1,0,0,0,1,1)."""
+    expect = np.diag([1, 1, 1, 1, 0, 0, 0, 1, 1]).astype(float)
+    np.testing.assert_allclose(abs_A(np.array([1.0, 0, 0])), expect, atol=1e-14)
+    np.testing.assert_allclose(abs_A(np.array([-1.0, 0, 0])), expect, atol=1e-14)
+
+
+def test_absA_invariants():
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        n = rng.standard_normal(3)
+        n /= np.linalg.norm(n)
+        A = A_of(n)
+        M = abs_A(n)
+        np.testing.assert_allclose(M @ M, A @ A, atol=1e-13)
+        assert np.min(np.linalg.eigvalsh(M)) > -1e-13
+        np.testing.assert_allclose(M, M.T, atol=1e-14)
+        # three zero eigenvalues (rank-6 A), the rest in +- pairs
+        ev = np.sort(np.linalg.eigvalsh(A))
+        np.testing.assert_allclose(ev, -ev[::-1], atol=1e-13)
+        assert np.sum(np.abs(ev) < 1e-12) == 3
+
+
+def test_hdg_flux_conservation_and_scalar_upwind():
+    """eq. HDGeqn: F_hat.n^- + F_hat.n^+ = 0 on a face; for m = 1 transport the
+    flux is the textbook upwind value beta.n u_upwind."""
+    rng = np.random.default_rng(2)
+    n = rng.standard_normal(3)
+    n /= np.linalg.norm(n)
+    um, up = rng.standard_normal(9), rng.standard_normal(9)
+    An, S = A_of(n), abs_A(n)
+    f_minus = hdg_flux(An, S, um, weighted_trace(An, S, um, up))
+    f_plus = hdg_flux(-An, S, up, weighted_trace(-An, S, up, um))
+    np.testing.assert_allclose(f_minus + f_plus, 0.0, atol=1e-13)
+    for b in (0.7, -0.3):
+        a = np.array([[b]])
+        s = np.array([[abs(b)]])
+        ul, ur = np.array([1.3]), np.array([-0.4])
+        f = hdg_flux(a, s, ul, weighted_trace(a, s, ul, ur))
+        assert abs(f[0] - b * (ul[0] if b > 0 else ur[0])) < 1e-15
+
+
+# ---------------------------------------------------------------- LSRK(5,4)
+def _butcher_from_2n(A, B):
+    s = len(A)
+    # Track stage inputs Y_i and the register dU as coefficient vectors over k_j.
+    U = [Fraction(0)] * s
+    dU = [Fraction(0)] * s
+    rows = []
+    for i in range(s):
+        rows.append(list(U))                       # Y_i = U (before stage i)
+        dU = [A[i] * c for c in dU]
+        dU[i] += 1
+        U = [U[j] + B[i] * dU[j] for j in range(s)]
+    return rows, U
+
+
+def test_lsrk_order_conditions():
+    a, b = _butcher_from_2n(oracle.LSRK_A, oracle.LSRK_B)
+    s = len(b)
+    c = [sum(row) for row in a]
+    tol = Fraction(1, 10 ** 18)
+    conds = [
+        (sum(b), Fraction(1)),
+        (sum(b[i] * c[i] for i in range(s)), Fraction(1, 2)),
+        (sum(b[i] * c[i] ** 2 for i in range(s)), Fraction(1, 3)),
+        (sum(b[i] * a[i][j] * c[j] for i in range(s) for j in range(s)), Fraction(1, 6)),
+        (sum(b[i] * c[i] ** 3 for i in range(s)), Fraction(1, 4)),
+        (sum(b[i] * c[i] * a[i][j] * c[j] for i in range(s) for j in range(s)), Fraction(1, 8)),
+        (sum(b[i] * a[i][j] * c[j] ** 2 for i in range(s) for j in range(s)), Fraction(1, 12)),
+        (sum(b[i] * a[i][j] * a[j][k] * c[k] for i in range(s) for j in range(s) for k in range(s)),
+         Fraction(1, 24)),
+    ]
+    for got, want in conds:
+        assert abs(got - want) < tol
+    for ci, cc in zip(c, oracle.LSRK_C):
+        assert abs(ci - cc) < tol
+    # and it is not fifth order (discriminating)
+    assert abs(sum(b[i] * c[i] ** 4 for i in range(s)) - Fraction(1, 5)) > Fraction(1, 10 ** 6)
+
+
+def test_lsrk_temporal_order_four():
+    lam = np.array([[-0.5, 2.0], [-2.0, -0.5]])       # damped rotation y' = lam y
+    y0 = np.array([1.0, 0.0])
+    exact_T = None
+    errs = []
+    for nsteps in (20, 40, 80):
+        dt = 1.0 / nsteps
+        y, res = y0.copy(), np.zeros(2)
+        for _ in range(nsteps):
+            for s in range(5):
+                res = float(oracle.LSRK_A[s]) * res + dt * (lam @ y)
+                y = y + float(oracle.LSRK_B[s]) * res
+        w, V = np.linalg.eig(lam)
+        exact_T = np.real(V @ np.diag(np.exp(w)) @ np.linalg.solve(V, y0))
+        errs.append(np.linalg.norm(y - exact_T))
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(rates > 3.8) and np.all(rates < 4.5)
+
+
+# ------------------------------------------------------------------- CFL pin
+def test_cfl_matches_paper_table():
+    rows = np.loadtxt(os.path.join(GOLDEN, "cfl_time_dependent_transport.txt"))
+    for cores, nel, printed in rows:
+        E = round(nel ** (1 / 3))
+        assert E ** 3 == nel
+        cfl = oracle.cfl_number(0.01, 1.0 / E, 0.35, 4)
+        assert abs(cfl - printed) <= 0.05 * printed + 1e-12
+        assert abs(oracle.cfl_dt(cfl, 1.0 / E, 0.35, 4) - 0.01) < 1e-15
+
+
+# -------------------------------------------------------------- geometry pins
+def _operator(E, N, a, periodic=(True, True, True), boundary=None, tau=1, rotate=None, mat=None):
+    r, _ = oracle.gll(N)
+    mesh = wl.structured_hex_mesh(E, periodic, boundary)
+    if rotate is not None:
+        mesh = wl.rotate_elements(mesh, rotate)
+    x = wl.warped_node_coords(mesh, r, a)
+    if mat is None:
+        rho, lam, mu = wl.homogeneous_material(mesh.nel)
+    else:
+        rho, lam, mu = wl.smooth_random_material(mesh, mat)
+    op = ElasticDG(N, x, mesh.etoe, mesh.etof, mesh.orient, mesh.bc, rho, lam, mu, tau)
+    return op, mesh, x
+
+
+def _analytic_metrics(X0, a):
+    """Exact J a^i_k and J of the warp x -> X0 + a prod sin(2 pi X0), from the
+    cofactors of its Jacobian matrix, for a cube element of edge h: X0 = c + (xi+1) h/2."""
+    s = np.sin(2 * np.pi * X0)
+    c = np.cos(2 * np.pi * X0)
+    grad = np.stack([2 * np.pi * c[..., 0] * s[..., 1] * s[..., 2],
+                     2 * np.pi * s[..., 0] * c[..., 1] * s[..., 2],
+                     2 * np.pi * s[..., 0] * s[..., 1] * c[..., 2]], axis=-1)
+    F = np.eye(3) + a * np.ones(3)[:, None] * grad[..., None, :]   # dx_i/dX0_j
+    return F
+
+
+@pytest.mark.parametrize("a", [0.05, 0.1])
+def test_curl_metrics_match_cofactors(a):
+    E, N = 2, 10
+    op, mesh, x = _operator(E, N, a)
+    elems = np.arange(op.nel)
+    Ja, J = op.geometry(elems)
+    r = op.r
+    rho = wl.mesh.reference_grid(r)
+    h = 1.0 / E
+    X0 = (mesh.cell[:, None, :] + (rho[None] + 1) / 2) / E
+    F = _analytic_metrics(X0, a) * (h / 2)                 # dx/dxi
+    J_exact = np.linalg.det(F)
+    cof = np.linalg.inv(F) * J_exact[..., None, None]      # J dxi_i/dx_k
+    np.testing.assert_allclose(J, J_exact, rtol=0, atol=1e-5 * np.max(J_exact))
+    for i in range(3):
+        for k in range(3):
+            np.testing.assert_allclose(Ja[i][k], cof[..., i, k], atol=1e-5 * (h / 2) ** 2)
+
+
+def test_discrete_metric_identities_and_positive_J():
+    op, mesh, x = _operator(3, 4, 0.1)
+    elems = np.arange(op.nel)
+    Ja, J = op.geometry(elems)
+    assert np.all(J > 0)
+    for k in range(3):
+        div = sum(op.dref(Ja[i][k], i) for i in range(3))
+        assert np.max(np.abs(div)) < 1e-13
+
+
+def test_flat_boundary_face_area():
+    """The warp vanishes on the cube's faces: the z=0 face has area exactly 1."""
+    op, mesh, x = _operator(3, 4, 0.1, periodic=(True, True, False),
+                            boundary={4: wl.BC_ABSORBING, 5: wl.BC_FREE_SURFACE})
+    elems = np.nonzero(mesh.bc[:, 4] == wl.BC_ABSORBING)[0]
+    Ja, J = op.geometry(elems)
+    m = op.outward_scaled_normal(Ja, 4)
+    sJ = np.linalg.norm(m, axis=-1)
+    area = np.sum(op.w_face[None, :] * sJ)
+    assert abs(area - 1.0) < 1e-12
+    np.testing.assert_allclose(m[..., 2] / sJ, -1.0, atol=1e-12)
+
+
+def test_matched_face_nodes_coincide():
+    """Neighbour maps (including all eight permutation codes on a rotated mesh)
+    pair physically coincident nodes (modulo the periodic shift)."""
+    for rotate in (None, 7):
+        op, mesh, x = _operator(3, 3, 0.1, rotate=rotate)
+        flat = x.reshape(-1, 3)
+        for f in range(6):
+            nbr = op._neighbour_map(f)
+            own = x[:, op.face_nodes[f]]                    # [nel, nf, 3]
+            other = flat[nbr]
+            d = own - other
+            d -= np.round(d)                                 # periodic shift by whole cube
+            assert np.max(np.abs(d)) < 1e-12
+        if rotate is not None:
+            assert len(set(mesh.orient.ravel().tolist())) == 8
+
+
+# --------------------------------------------------- free stream / constants
+@pytest.mark.parametrize("rotate", [None, 3])
+def test_free_stream_preservation(rotate):
+    op, mesh, x = _operator(3, 4, 0.1, rotate=rotate)
+    u = np.ones((9, op.nel, op.Np)) * np.arange(1, 10)[:, None, None]
+    L = op.rhs(u)
+    assert np.max(np.abs(L)) < 1e-11 * np.max(np.abs(u)) * (op.N ** 2 * 3)
+
+
+# ------------------------------------------------------------ energy identity
+@pytest.mark.parametrize("tau", [0, 1])
+def test_semidiscrete_energy_identity_periodic(tau):
+    op, mesh, x = _operator(3, 3, 0.1, tau=tau, mat=4)
+    u = wl.random_state(op.nel, op.Np, 11)
+    rate = op.energy_rate(u)
+    faces = op.energy_rate_from_faces(u)
+    scale = op.energy(u) * op.N ** 2 * 3 / 0.2
+    if tau == 0:
+        assert abs(rate) < 1e-12 * scale
+    else:
+        assert faces < 0
+    assert abs(rate - faces) < 1e-12 * scale
+
+
+def test_semidiscrete_energy_identity_boundaries():
+    op, mesh, x = _operator(3, 3, 0.1, periodic=(True, False, False),
+                            boundary={2: wl.BC_FREE_SURFACE, 3: wl.BC_ABSORBING,
+                                      4: wl.BC_ABSORBING, 5: wl.BC_FREE_SURFACE}, mat=5)
+    u = wl.random_state(op.nel, op.Np, 12)
+    rate = op.energy_rate(u)
+    faces = op.energy_rate_from_faces(u)
+    scale = op.energy(u) * op.N ** 2 * 3 / 0.2
+    assert faces < 0
+    assert abs(rate - faces) < 1e-12 * scale
+
+
+def test_free_surface_central_conserves_energy():
+    """With the central flux a traction-free surface neither adds nor removes energy."""
+    op, mesh, x = _operator(2, 3, 0.05, periodic=(True, True, False),
+                            boundary={4: wl.BC_FREE_SURFACE, 5: wl.BC_FREE_SURFACE}, tau=0, mat=6)
+    u = wl.random_state(op.nel, op.Np, 13)
+    scale = op.energy(u) * op.N ** 2 * 2 / 0.5
+    assert abs(op.energy_rate(u)) < 1e-12 * scale
+
+
+# --------------------------------------------------- brute-force operator
+@pytest.mark.parametrize("E,N,tau", [(1, 2, 0), (1, 2, 1), (2, 1, 0), (2, 1, 1)])
+def test_bruteforce_operator_skew_and_dissipative(E, N, tau):
+    op, mesh, x = _operator(E, N, 0.08, tau=tau, mat=8)
+    n = 9 * op.nel * op.Np
+    L = np.zeros((n, n))
+    for c in range(n):
+        e = np.zeros(n)
+        e[c] = 1.0
+        L[:, c] = op.rhs(e.reshape(9, op.nel, op.Np)).ravel()
+    _, J = op.geometry(np.arange(op.nel))
+    MQ = np.zeros((n, n))
+    for el in range(op.nel):
+        Q = oracle.Q_of(op.rho[el], op.lam[el], op.mu[el])
+        for p in range(9):
+            for q in range(9):
+                idx_p = p * op.nel * op.Np + el * op.Np + np.arange(op.Np)
+                idx_q = q * op.nel * op.Np + el * op.Np + np.arange(op.Np)
+                MQ[idx_p, idx_q] = Q[p, q] * op.w_vol * J[el]
+    S = MQ @ L
+    sym = S + S.T
+    scale = np.max(np.abs(S))
+    if tau == 0:
+        assert np.max(np.abs(sym)) < 1e-12 * scale
+    else:
+        assert np.max(np.linalg.eigvalsh(0.5 * sym)) < 1e-12 * scale
+        assert np.min(np.linalg.eigvalsh(0.5 * sym)) < -1e-3 * scale
+    ev = np.linalg.eigvals(L)
+    assert np.max(ev.real) < 1e-10 * np.max(np.abs(ev))
+
+
+# --------------------------------------------------- plane wave: sign + order
+def test_plane_wave_time_derivative():
+    """The operator applied to the exact plane P-wave gives its time derivative."""
+    op, mesh, x = _operator(2, 8, 0.05)
+    u0 = wl.plane_p_wave(x, 1.0, 2.0, 1.0, t=0.0)
+    dt = 1e-5
+    dudt = (wl.plane_p_wave(x, 1.0, 2.0, 1.0, t=dt) - wl.plane_p_wave(x, 1.0, 2.0, 1.0, t=-dt)) / (2 * dt)
+    L = op.rhs(u0)
+    err = np.linalg.norm(L - dudt) / np.linalg.norm(dudt)
+    assert err < 1e-3
+
+
+def _l2_error(op, u, uex):
+    _, J = op.geometry(np.arange(op.nel))
+    d = u - uex
+    return np.sqrt(np.sum(op.w_vol * J * np.sum(d * d, axis=0)))
+
+
+@pytest.mark.parametrize("N,meshes,min_rate", [(2, (4, 8), 2.4), (4, (2, 4), 4.0)])
+def test_plane_wave_design_order(N, meshes, min_rate):
+    """L2 error at T of the plane P-wave on the warped periodic mesh falls at
+    close to the design rate N+1 (pre-asymptotic meshes: the bound is N+0.4 / N)."""
+    T = 0.05
+    errs = []
+    for E in meshes:
+        op, mesh, x = _operator(E, N, 0.05)
+        u = wl.plane_p_wave(x, 1.0, 2.0, 1.0, direction=(1, 0, 0))
+        dt0 = oracle.cfl_dt(0.5, 1.0 / E, 2.0, N)
+        nsteps = int(np.ceil(T / dt0))
+        dt = T / nsteps
+        res = np.zeros_like(u)
+        for _ in range(nsteps):
+            u, res = op.step(u, res, dt)
+        errs.append(_l2_error(op, u, wl.plane_p_wave(x, 1.0, 2.0, 1.0, t=T, direction=(1, 0, 0))))
+    rate = np.log2(errs[0] / errs[1])
+    assert rate > min_rate, (errs, rate)
+
+
+# ------------------------------------------------------- fully discrete energy
+def test_energy_nonincreasing_parity_workload():
+    cfg = wl.parity_config()
+    r, _ = oracle.gll(cfg.N)
+    d = cfg.build(r)
+    m = d["mesh"]
+    op = ElasticDG(cfg.N, d["x"], m.etoe, m.etof, m.orient, m.bc, d["rho"], d["lam"], d["mu"], cfg.tau)
+    dt = oracle.cfl_dt(cfg.cfl, 1.0 / cfg.E, op.c_max(), cfg.N)
+    assert abs(dt - 0.5 * 0.25 / (2.0 * 9)) < 1e-15
+    u, res = d["u0"], np.zeros_like(d["u0"])
+    E0 = op.energy(u)
+    prev = E0
+    for _ in range(20):
+        u, res = op.step(u, res, dt)
+        En = op.energy(u)
+        assert En <= prev * (1 + 1e-13)
+        prev = En
+    assert prev > 0.5 * E0
+
+
+def test_free_surface_numerical_traction_vanishes():
+    """On a traction-free face the HDG flux carries no traction: the velocity rows
+    of F_hat.n (= -sigma_hat n) are zero for any interior state."""
+    op, mesh, x = _operator(2, 3, 0.1, periodic=(True, True, False),
+                            boundary={4: wl.BC_ABSORBING, 5: wl.BC_FREE_SURFACE}, mat=9)
+    u = wl.random_state(op.nel, op.Np, 14)
+    elems = np.nonzero(mesh.bc[:, 5] == wl.BC_FREE_SURFACE)[0]
+    Ja, J = op.geometry(elems)
+    m = op.outward_scaled_normal(Ja, 5)
+    nrm = m / np.linalg.norm(m, axis=-1)[..., None]
+    um, up = op.exterior_state(u, elems, 5)
+    um, up = np.moveaxis(um, 0, -1), np.moveaxis(up, 0, -1)
+    An = np.einsum("...k,kij->...ij", nrm, oracle.dg_elastic.A_STACK)
+    S = abs_A(nrm)
+    F = hdg_flux(An, S, um, weighted_trace(An, S, um, up))
+    assert np.max(np.abs(F[..., :3])) < 1e-13
+    assert np.max(np.abs(F[..., 3:])) > 1e-3
