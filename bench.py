@@ -1,0 +1,413 @@
+"""Throughput of the DG elastic-wave hot path on the large workload.
+
+One bench step = one LSRK(5,4) step (five fused stage launches through the C
+ABI's dgw_stage, ping-ponging two state buffers) plus one dgw_energy call,
+over the 64^3-element, N=4 curvilinear mesh with the smooth random medium.
+Metric: DOF-stage-updates/s = nel * Np * 9 * 5 * steps / time.
+
+Default run: the FP64 path (every operation in FP64) is the headline line;
+the mixed path (FP32 volume/flux/lift, FP64 Runge-Kutta registers and
+energy) is reported in ``variants.mixed``.  ``--impl reference`` times the
+CPU oracle on a bounded sample of the same workload instead.
+
+Multi-GPU (torchrun): the path is replicated, one independent solve per rank
+("replicas only": no data-path collective); value = all ranks' updates / the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import os
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")     # the CPU baseline is single-threaded
+
+import argparse
+import json
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as wl  # noqa: E402
+
+METRIC = "DOF-stage-updates/s on 1 GB300 (FP64 vs mixed) + %HBM roofline; served p99 ms"
+UNIT = "DOF-stage-updates/s"
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# FP64 peak: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz (nominal 1.26 TFLOP/s).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def algorithmic_bytes_per_dof(N, real_bytes):
+    """Minimum HBM traffic of one fused stage per DOF: u in, res in/out, u out
+    (FP64, 32 B); 10 geometry values per node (Ja, 1/J); 4 face values (n, sJ)
+    per node of the three faces an element owns."""
+    n = N + 1
+    Np = n ** 3
+    return 32.0 + 10.0 * real_bytes / 9.0 + 3 * n * n * 4 * real_bytes / (9.0 * Np)
+
+
+def algorithmic_flops_per_element(N):
+    """Flops of one fused stage per element as the kernel's arithmetic is written:
+    per node and direction, A(m)u (27), two length-(N+1) contractions of 9 fields
+    (36(N+1)), A(m) du (27) and two 9-wide accumulations (18); volume scale (10),
+    Q^{-1} (14) and the LSRK update (45) per node; per face node the flux
+    difference (jump 9, A(m) 27, |A(m)| 42, scaling 27) and its lift (9)."""
+    n = N + 1
+    Np, nf = n ** 3, n * n
+    per_node = 3 * (27 + 36 * n + 27 + 18) + 10 + 14 + 45
+    per_face_node = 9 + 27 + 42 + 27 + 9
+    return Np * per_node + 6 * nf * per_face_node
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        rows = [l.split(",") for l in open(self.path).read().strip().splitlines() if l.strip()]
+        os.unlink(self.path)
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            if len(r) < 9:
+                continue
+            for nm, val in zip(names, r[5:9]):
+                if val.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def build_workload(E, N):
+    cfg = wl.large_config(E=E, N=N)
+    from paper_1711_01175_gb300 import reference_nodes
+    r, _ = reference_nodes(N)
+    data = cfg.build(r)
+    return cfg, data
+
+
+def setup_solver(precision, cfg, data):
+    from paper_1711_01175_gb300 import Solver
+    m = data["mesh"]
+    s = Solver(cfg.N, tau=cfg.tau, precision=precision, cfl=cfg.cfl)
+    s.upload_mesh(data["x"], m.etoe, m.etof, m.orient, m.bc)
+    s.upload_material(data["rho"], data["lam"], data["mu"])
+    return s
+
+
+def run_variant(precision, cfg, data, steps, warmup, device, stream, clocks=None):
+    """Device-resident timing: K steps of 5 stage launches + 1 energy launch pair."""
+    import torch
+    from paper_1711_01175_gb300 import capi
+    s = setup_solver(precision, cfg, data)
+    nel, Np = data["mesh"].nel, (cfg.N + 1) ** 3
+    dt = s.dt_cfl()
+    with torch.cuda.stream(stream):
+        ua = torch.from_numpy(data["u0"]).to(device)
+        ub = torch.empty_like(ua)
+        res = torch.zeros_like(ua)
+    h = capi._P(stream.cuda_stream)
+    ctx = s._ctx
+    lib = capi.load()
+    energies = []
+
+    def one_step(record=None):
+        nonlocal ua, ub
+        if record is not None:
+            record[0].record(stream)
+        for st in range(5):
+            capi.check(lib.dgw_stage(ctx, ua.data_ptr(), ub.data_ptr(), res.data_ptr(), st, 0.0, dt, h), ctx)
+            ua, ub = ub, ua
+        if record is not None:
+            record[1].record(stream)
+        e = capi.dgw_energy(ctx, ua.data_ptr(), h)
+        capi.check(e[0], ctx)
+        energies.append(e[1])
+
+    for _ in range(warmup):
+        one_step()
+    torch.cuda.synchronize(device)
+    if torch.distributed.is_initialized():
+        torch.distributed.barrier()
+    torch.cuda.synchronize(device)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    if clocks:
+        clocks.start()
+    t0.record(stream)
+    for k in range(steps):
+        one_step(ev[k])
+    t1.record(stream)
+    torch.cuda.synchronize(device)
+    clk = clocks.stop() if clocks else None
+    total_ms = t0.elapsed_time(t1)
+    stage_ms = sum(a.elapsed_time(b) for a, b in ev) / (5 * steps)
+    dof = nel * Np * 9
+    out = {
+        "total_ms": total_ms, "ms_per_step": total_ms / steps, "stage_ms": stage_ms,
+        "dof": dof, "nel": nel, "Np": Np, "energy_first": energies[0], "energy_last": energies[-1],
+        "clocks": clk,
+    }
+    del ua, ub, res
+    s.close()
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_e2e(precision, cfg, data, steps, warmup, device, stream):
+    """Through the public call with pinned host buffers: dgw_step(host u, res, 1 step)
+    copies in, runs, copies back; then dgw_energy(host u)."""
+    import torch
+    s = setup_solver(precision, cfg, data)
+    dt = s.dt_cfl()
+    u = torch.from_numpy(data["u0"]).pin_memory()
+    res = torch.zeros_like(u).pin_memory()
+    nbytes = u.numel() * 8
+    with torch.cuda.stream(stream):
+        for _ in range(max(1, min(warmup, 2))):
+            s.step(u, res, dt, 1, stream=stream)
+            s.energy(u, stream=stream)
+        torch.cuda.synchronize(device)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(steps):
+            s.step(u, res, dt, 1, stream=stream)
+            s.energy(u, stream=stream)
+        t1.record(stream)
+        torch.cuda.synchronize(device)
+    ms = t0.elapsed_time(t1)
+    s.close()
+    return {"ms": ms, "h2d_bytes_per_step": 3 * nbytes, "d2h_bytes_per_step": 2 * nbytes + 8}
+
+
+def cpu_oracle_sample(cfg, data, target_s=12.0, nel_sample=512):
+    """The oracle, as it stands, on a bounded sample: LSRK stages of the large
+    workload computed for a contiguous block of elements (single thread)."""
+    import oracle
+    m = data["mesh"]
+    r, _ = oracle.gll(cfg.N)
+    x = wl.warped_node_coords(m, r, cfg.amplitude)
+    op = oracle.ElasticDG(cfg.N, x, m.etoe, m.etof, m.orient, m.bc, data["rho"], data["lam"], data["mu"], cfg.tau)
+    dt = oracle.cfl_dt(cfg.cfl, oracle.h_min_corner_edges(x, cfg.N), op.c_max(), cfg.N)
+    elems = np.arange(min(nel_sample, m.nel))
+    u = data["u0"]
+    res = np.zeros_like(u)
+    op.lsrk_stage(u, res, 0, dt, elems)          # geometry of the sample (set-up, untimed)
+    stages = 0
+    t0 = time.perf_counter()
+    while True:
+        for s_ in range(5):
+            op.lsrk_stage(u, res, s_, dt, elems)
+            stages += 1
+        if time.perf_counter() - t0 > target_s:
+            break
+    el = time.perf_counter() - t0
+    Np = (cfg.N + 1) ** 3
+    return {"value": len(elems) * Np * 9 * stages / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{stages} LSRK stages on {len(elems)} of {m.nel} elements of {cfg.name} "
+                      f"(numpy FP64, 1 thread), {el:.1f} s"}
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    E, N = args.elements, 4
+    cfg, data = build_workload_oracle(E, N)
+    per_step = []
+    total_units = 0
+    import oracle
+    m = data["mesh"]
+    r, _ = oracle.gll(N)
+    x = wl.warped_node_coords(m, r, cfg.amplitude)
+    op = oracle.ElasticDG(N, x, m.etoe, m.etof, m.orient, m.bc, data["rho"], data["lam"], data["mu"], cfg.tau)
+    dt = oracle.cfl_dt(cfg.cfl, oracle.h_min_corner_edges(x, N), op.c_max(), N)
+    elems = np.arange(args.ref_sample)
+    u, res = data["u0"], np.zeros_like(data["u0"])
+    Np = (N + 1) ** 3
+    op.lsrk_stage(u, res, 0, dt, elems)          # geometry of the sample (set-up, untimed)
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        for s_ in range(5):
+            op.lsrk_stage(u, res, s_, dt, elems)
+        el = time.perf_counter() - t0
+        if k >= args.warmup:
+            per_step.append(el)
+            total_units += len(elems) * Np * 9 * 5
+    tt = sum(per_step)
+    value = total_units / tt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": cfg.name, "elements": m.nel, "N": N,
+                       "sample_elements": len(elems)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"one LSRK step (5 stages) per bench step on {len(elems)} of "
+                                       f"{m.nel} elements (numpy FP64, 1 thread)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def build_workload_oracle(E, N):
+    import oracle
+    cfg = wl.large_config(E=E, N=N)
+    r, _ = oracle.gll(N)
+    return cfg, cfg.build(r)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--precision", default="both", choices=["both", "fp64", "mixed"])
+    ap.add_argument("--elements", type=int, default=64, help="elements per axis (64: the large workload)")
+    ap.add_argument("--mixed-steps", type=int, default=None, help="steps for the mixed variant (default 4x)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ref-sample", type=int, default=256, help="elements per reference-arm step")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    stream = torch.cuda.Stream(device)
+
+    import __graft_entry__ as g
+    if rank == 0:
+        g.build()
+    if world > 1:
+        torch.distributed.barrier()
+    g.build()
+
+    cfg, data = build_workload(args.elements, 4)
+    hbm_peak, peak_kind = peaks()
+    variants = ["fp64", "mixed"] if args.precision == "both" else [args.precision]
+    results = {}
+    for prec in variants:
+        k = args.steps if prec == "fp64" else (args.mixed_steps or 4 * args.steps)
+        clk = Clocks(local)
+        r = run_variant(prec, cfg, data, k, args.warmup, device, stream, clk)
+        r["steps"] = k
+        total = torch.tensor([r["total_ms"]], device=device)
+        if world > 1:
+            torch.distributed.all_reduce(total, op=torch.distributed.ReduceOp.MAX)
+        r["max_ms"] = float(total.item())
+        r["value"] = world * r["dof"] * 5 * k / (r["max_ms"] * 1e-3)
+        if not args.no_e2e:
+            e = run_e2e(prec, cfg, data, max(2, k // 4), args.warmup, device, stream)
+            r["e2e"] = {"value": r["dof"] * 5 * max(2, k // 4) / (e["ms"] * 1e-3) * world, "unit": UNIT,
+                        "h2d_bytes_per_step": e["h2d_bytes_per_step"],
+                        "d2h_bytes_per_step": e["d2h_bytes_per_step"]}
+        launches_per_step = 5 + 2
+        r["gpu_launches"] = launches_per_step * k
+        N = cfg.N
+        if prec == "fp64":
+            flops = algorithmic_flops_per_element(N) * r["nel"]
+            ach = flops / (r["stage_ms"] * 1e-3) / 1e12
+            r["roofline"] = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                             "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                             "kernel": "stage_kernel<4,double,LSRK>",
+                             "note": "FP64 flops as written per launch / CUDA-event stage time; peak derived "
+                                     "from 152 SMs x 2 DFMA/clk x 2.07 GHz (nominal)"}
+        else:
+            nbytes = algorithmic_bytes_per_dof(N, 4) * r["dof"]
+            ach = nbytes / (r["stage_ms"] * 1e-3) / 1e9
+            r["roofline"] = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                             "frac": ach / hbm_peak, "traffic": None,
+                             "kernel": "stage_kernel<4,float,LSRK>",
+                             "note": f"algorithmic bytes {algorithmic_bytes_per_dof(N, 4):.2f} B/DOF; "
+                                     f"peak {peak_kind} copy bandwidth"}
+        results[prec] = r
+
+    if rank != 0:
+        torch.distributed.destroy_process_group() if world > 1 else None
+        return
+    head = results.get("fp64") or results["mixed"]
+    head_prec = "fp64" if "fp64" in results else "mixed"
+    line = {
+        "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": head["steps"],
+        "warmup": args.warmup, "ms_per_step": head["max_ms"] / head["steps"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if head_prec == "fp64" else "f32/f64",
+        "data": "synthetic (seeded mesh, medium and Gaussian pulse of the large workload)",
+        "config": {"workload": cfg.name + " (64^3 hex, N=4, warp 0.1, smooth random medium, free surface top, "
+                   "absorbing bottom, x/y periodic)", "precision": head_prec, "elements": head["nel"],
+                   "dof": head["dof"], "step": "one LSRK(5,4) step (5 fused stage launches) + one energy",
+                   "l2": "inputs larger than L2 (state 2.36 GB per buffer)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": head["roofline"],
+        "clocks": head["clocks"],
+        "gpu_launches": head["gpu_launches"],
+    }
+    if "e2e" in head:
+        line["e2e"] = head["e2e"]
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_oracle_sample(cfg, data)
+    if len(results) > 1:
+        m = results["mixed"]
+        line["variants"] = {"mixed": {"value": m["value"], "dtype": "f32/f64", "steps": m["steps"],
+                                      "ms_per_step": m["max_ms"] / m["steps"], "roofline": m["roofline"],
+                                      "clocks": m["clocks"], "e2e": m.get("e2e"),
+                                      "gpu_launches": m["gpu_launches"]}}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

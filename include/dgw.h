@@ -1,0 +1,160 @@
+/*
+ * dgw.h -- C ABI of the GB300 DG elastic-wave hot path.
+ *
+ * The library evaluates the semi-discrete upwind DG operator of a linear
+ * Friedrichs system (the paper's Section 2, eq. LPDE, with m = 9 unknowns:
+ * velocity-stress elasticity, Q du/dt + sum_k d_k(A_k u) = 0) on curvilinear
+ * hexahedra, and advances it with a five-stage low-storage Runge-Kutta
+ * method.  The numerical flux is the upwind HDG flux (eq. RiemannFluxBoth)
+ * with the trace eliminated through the face conservation condition
+ * (eq. HDGeqn, in the form of eq. iHDGtrace); the time scheme is the paper's
+ * element-by-element explicit HDG scheme (Section 4.2) with LSRK(5,4) in place
+ * of forward Euler.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * N      polynomial degree per axis (1..7); n = N+1 GLL nodes per axis,
+ *        Np = n^3 nodes per element, nf = n^2 nodes per face.
+ * node   index i + n*(j + n*k) of reference node (r_i, s_j, t_k); r fastest.
+ * faces  0: r=-1, 1: r=+1, 2: s=-1, 3: s=+1, 4: t=-1, 5: t=+1.
+ * state  u[9][nel][Np], FP64, fields (v1, v2, v3, s11, s22, s33, s23, s13, s12).
+ *
+ * Errors: every call returns a dgw_status and never aborts or throws.  A
+ * failing call leaves a message retrievable with dgw_last_error(ctx).  Calls
+ * on one context are not thread safe; distinct contexts are independent.
+ * Device work is enqueued on the caller's stream (a cudaStream_t passed as
+ * void*, NULL = legacy default stream).  Pointers to field buffers may be
+ * device memory (the call is asynchronous on the stream) or host memory (the
+ * call stages the data through context-owned device buffers and returns after
+ * the copies back to the host have completed).  The library never frees
+ * caller memory.
+ */
+#ifndef DGW_H
+#define DGW_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dgw_ctx dgw_ctx;
+
+typedef enum {
+  DGW_OK = 0,
+  DGW_ERR_ARG = -1,         /* invalid argument (sizes, connectivity, J <= 0, material) */
+  DGW_ERR_STATE = -2,       /* calls out of order: create -> mesh -> material -> compute */
+  DGW_ERR_OOM = -3,         /* device allocation failed */
+  DGW_ERR_CUDA = -4,        /* a CUDA runtime call failed */
+  DGW_ERR_UNSTABLE = -5,    /* non-finite energy */
+  DGW_ERR_TIMEOUT = -6,     /* reserved for bounded device waits */
+  DGW_ERR_UNSUPPORTED = -7  /* configuration or call not built */
+} dgw_status;
+
+enum { DGW_PRECISION_FP64 = 0, DGW_PRECISION_MIXED = 1 };
+enum { DGW_BC_INTERIOR = 0, DGW_BC_FREE_SURFACE = 1, DGW_BC_ABSORBING = 2 };
+
+typedef struct {
+  int N;          /* polynomial degree, 1..7 */
+  int flux_tau;   /* 0: central flux (stabilisation dropped), 1: upwind HDG flux */
+  int precision;  /* DGW_PRECISION_FP64: every operation in FP64.
+                     DGW_PRECISION_MIXED: volume, flux and lift in FP32 with FP32
+                     geometry; the Runge-Kutta registers and energy stay FP64. */
+  double cfl;     /* CFL number used by dgw_dt_cfl */
+} dgw_config;
+
+/* ABI version of this header (bumped on any signature change). */
+#define DGW_ABI_VERSION 1
+int dgw_abi_version(void);
+
+/* GLL nodes r[0..N] (ascending, r[0] = -1, r[N] = +1) and weights w[0..N]
+ * that the library uses; node coordinates passed to dgw_mesh_upload must be
+ * given at these reference positions.  r, w: host arrays of N+1 doubles,
+ * caller-owned.  DGW_ERR_ARG if N is outside 1..7 or a pointer is NULL. */
+dgw_status dgw_reference_nodes(int N, double* r, double* w);
+
+/* Create a context on CUDA device `device`.  *out receives an opaque handle
+ * that owns all geometry, material and scratch device memory; release it
+ * with dgw_destroy.  DGW_ERR_ARG for a bad config, DGW_ERR_CUDA if the device
+ * cannot be used. */
+dgw_status dgw_create(dgw_ctx** out, int device, const dgw_config* cfg);
+
+/* Free every resource of the context (NULL is accepted). */
+dgw_status dgw_destroy(dgw_ctx* ctx);
+
+/* Mesh and skeleton (Section 2: elements K_j, faces of the skeleton, outward
+ * normals n^- and n^+ = -n^-).  All arrays are host, caller-owned, read
+ * during the call only:
+ *   x      [nel][Np][3] physical coordinates of the element nodes at the
+ *          reference positions of dgw_reference_nodes; faces shared by two
+ *          elements must carry coincident nodes;
+ *   etoe   [nel][6] neighbour element across each local face, -1 on a
+ *          physical boundary (periodic meshes list the periodic neighbour);
+ *   etof   [nel][6] the neighbour's local face (ignored where etoe = -1);
+ *   orient [nel][6] face-node permutation 0..7: own face-local (a, b) (a along
+ *          the lower-numbered tangential axis) meets neighbour (a', b') with
+ *          (a1, b1) = (o & 1) ? (b, a) : (a, b), a' = (o & 2) ? N - a1 : a1,
+ *          b' = (o & 4) ? N - b1 : b1;
+ *   bc     [nel][6] DGW_BC_INTERIOR where etoe >= 0, otherwise
+ *          DGW_BC_FREE_SURFACE (traction-free: exterior state (v, -sigma)) or
+ *          DGW_BC_ABSORBING (exterior state 0).
+ * The call computes the curl-form metric terms, Jacobians, face normals and
+ * face stabilisation matrices on the device.  DGW_ERR_ARG (message names the
+ * element) if the connectivity is not symmetric, a tag is inconsistent, or
+ * J <= 0 at some node; nel * Np must be below 2^31.  May be called again to
+ * replace the mesh (material must then be uploaded again). */
+dgw_status dgw_mesh_upload(dgw_ctx* ctx, int64_t nel, const double* x, const int64_t* etoe,
+                           const int8_t* etof, const int8_t* orient, const int8_t* bc);
+
+/* Per-element isotropic medium: density rho, Lame parameters lam and mu (host
+ * [nel] arrays, caller-owned).  The medium enters only the time weight
+ * Q = diag(rho I, C_V^{-1}).  DGW_ERR_ARG unless rho > 0, mu > 0 and
+ * lam > -2/3 mu everywhere.  DGW_ERR_STATE before dgw_mesh_upload. */
+dgw_status dgw_material_upload(dgw_ctx* ctx, const double* rho, const double* lam, const double* mu);
+
+/* rhs = L(u) = Q^{-1} [ split-form volume term + lifted upwind flux
+ * difference ] for every element (the explicit HDG right-hand side, Section
+ * 4.2, with the flux of eq. RiemannFluxBoth).  u: [9][nel][Np] input, rhs:
+ * [9][nel][Np] output, both FP64, must not overlap.  t is the stage time (no
+ * time-dependent terms are active; kept for sources). */
+dgw_status dgw_rhs(dgw_ctx* ctx, const double* u, double* rhs, double t, void* stream);
+
+/* One fused LSRK stage s (0..4):  res <- a_s res + dt L(u_in);
+ * u_out <- u_in + b_s res.  u_in and u_out must be distinct buffers (the
+ * face gather reads neighbours of u_in while u_out is written); res is read
+ * and written in place.  Device pointers only. */
+dgw_status dgw_stage(dgw_ctx* ctx, const double* u_in, double* u_out, double* res, int stage,
+                     double t, double dt, void* stream);
+
+/* nsteps LSRK(5,4) steps of size dt from time t0, in place on u and res
+ * (res must hold zeros, or the register of the previous step -- its value is
+ * multiplied by a_0 = 0).  Uses a context-owned second state buffer for the
+ * stage ping-pong and copies the final state back into u. */
+dgw_status dgw_step(dgw_ctx* ctx, double* u, double* res, double t0, double dt, int nsteps,
+                    void* stream);
+
+/* Discrete energy E = 1/2 sum_K sum_nodes w J u^T Q u, accumulated in FP64
+ * with a fixed reduction order (bit-reproducible for a given mesh).
+ * energy_out: host double.  Synchronises the stream.  DGW_ERR_UNSTABLE if E
+ * is not finite (the value is still written). */
+dgw_status dgw_energy(dgw_ctx* ctx, const double* u, double* energy_out, void* stream);
+
+/* Adjoint of dgw_step with material gradients.  Not built yet: returns
+ * DGW_ERR_UNSUPPORTED. */
+dgw_status dgw_adjoint_step(dgw_ctx* ctx, double* lam_u, double* lam_res, double* grad_mat,
+                            const double* u_ckpt, double t0, double dt, int nsteps, void* stream);
+
+/* dt = cfl * h / (c_max * N^2) with h the smallest element edge length
+ * (distance between adjacent element corner nodes) and c_max the largest
+ * P-wave speed sqrt((lam + 2 mu) / rho); the CFL convention of the paper's
+ * time-dependent transport experiments (Section 6.1). */
+dgw_status dgw_dt_cfl(dgw_ctx* ctx, double* dt_out);
+
+/* Message of the last failing call on ctx (or of the last failing call
+ * without a context when ctx is NULL).  Never NULL; owned by the library. */
+const char* dgw_last_error(const dgw_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DGW_H */

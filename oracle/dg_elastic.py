@@ -9,8 +9,12 @@ deliberately slow and follows the method step by step:
   (eq. LPDE), sum_k d_k(A_k u) + C u = f, here written with a time derivative
   Q du/dt and m = 9 components (velocity, Voigt stress): A_k constant and
   symmetric, the medium only in Q, C = 0, f = 0.
-* Upwind HDG stabilisation |A| = R|S|R^{-1} of A(n) = sum_k A_k n_k is taken
-  literally from its eigen-decomposition (Section 2, eq. RiemannFluxBoth).
+* Upwind HDG stabilisation |A| = R|S|R^{-1} (Section 2, eq. RiemannFluxBoth)
+  is taken literally from an eigen-decomposition of the flux matrix of the
+  system written as du/dt + sum_k d_k(Q^{-1} A_k u) = 0, i.e. Q^{-1} A(n),
+  and multiplied back by Q for the Q-weighted equation; where the medium
+  jumps across a face (outside Section 2's continuity assumption) the two
+  sides' (rho, lambda, mu) are averaged.
 * The weighted trace |A| u_hat is computed from the face conservation
   condition (Section 2, eq. HDGeqn) in the form of Section 3, eq. iHDGtrace,
   with both sides at the same time level, and the HDG flux
@@ -21,8 +25,8 @@ deliberately slow and follows the method step by step:
 
 Readings where the paper is silent (each one is also listed in the design
 notes): GLL collocation with N+1 points per axis; strong form with the
-split (skew-symmetric) volume term; curl-form metric terms; material-free
-|A(n)| as the stabilisation; free-surface mirror state and zero absorbing
+split (skew-symmetric) volume term; curl-form metric terms; face-averaged
+medium in the stabilisation; free-surface mirror state and zero absorbing
 state; Carpenter-Kennedy (1994) LSRK(5,4) coefficients; CFL convention
 dt = CFL h / (c_max N^2), which reproduces the CFL column of the paper's
 weak-scaling table for time-dependent transport (Section 6.1).
@@ -148,6 +152,30 @@ def abs_A(n):
     A = np.stack([A_of(v) for v in n.reshape(-1, 3)]).reshape(lead + (9, 9))
     S, R = np.linalg.eigh(A)
     return np.einsum("...ij,...j,...kj->...ik", R, np.abs(S), R)
+
+
+def abs_A_Q(n, rho, lam, mu):
+    """Stabilisation for the Q-weighted system: Q |Q^{-1} A(n)| = Q R |S| R^{-1}.
+
+    eq. RiemannFluxBoth applied to the system in the form
+    du/dt + sum_k d_k(Q^{-1} A_k u) = 0, whose flux matrix is Q^{-1} A(n) with
+    real eigenvalues (+-cp, +-cs twice, 0 three times); the Q-weighted equation
+    then carries Q R|S|R^{-1}.  Computed stably: Q^{-1}A = Q^{-1/2} At Q^{1/2}
+    with At = Q^{-1/2} A Q^{-1/2} symmetric, so R = Q^{-1/2} V for At = V S V^T
+    and Q R|S|R^{-1} = Q^{1/2} V |S| V^T Q^{1/2}.  Vectorised over the leading
+    axes of n; rho, lam, mu broadcast against them."""
+    n = np.asarray(n, dtype=np.float64)
+    lead = n.shape[:-1]
+    rho, lam, mu = (np.broadcast_to(np.asarray(v, dtype=np.float64), lead).reshape(-1) for v in (rho, lam, mu))
+    A = np.einsum("kc,cij->kij", n.reshape(-1, 3), A_STACK)
+    Q = np.stack([Q_of(r_, l_, m_) for r_, l_, m_ in zip(rho, lam, mu)])
+    w, U = np.linalg.eigh(Q)
+    Qh = np.einsum("kij,kj,klj->kil", U, np.sqrt(w), U)
+    Qih = np.einsum("kij,kj,klj->kil", U, 1.0 / np.sqrt(w), U)
+    At = Qih @ A @ Qih
+    S, V = np.linalg.eigh(At)
+    out = Qh @ np.einsum("kij,kj,klj->kil", V, np.abs(S), V) @ Qh
+    return out.reshape(lead + (9, 9))
 
 
 def weighted_trace(An, stab, um, up):
@@ -284,10 +312,21 @@ class ElasticDG:
         d, side = f // 2, (-1 if f % 2 == 0 else 1)
         return side * np.moveaxis(Ja[d][:, :, self.face_nodes[f]], 0, -1)   # [ne, nf, 3]
 
+    def face_material(self, elems, f):
+        """(rho, lam, mu) on face f of each element: the average of the two sides
+        on interior faces (the medium may jump there), the element's own on
+        boundary faces."""
+        e2 = self.etoe[elems, f]
+        interior = (e2 >= 0) & (self.bc[elems, f] == 0)
+        other = np.where(interior, e2, elems)
+        return tuple(0.5 * (v[elems] + v[other]) for v in (self.rho, self.lam, self.mu))
+
     def _abs_A_cached(self, elems, f, nrm):
         key = (elems.tobytes(), f)
         if key not in self._abs_cache:
-            self._abs_cache[key] = abs_A(nrm)
+            rho, lam, mu = self.face_material(elems, f)
+            shape = nrm.shape[:-1]
+            self._abs_cache[key] = abs_A_Q(nrm, *(np.broadcast_to(v[:, None], shape) for v in (rho, lam, mu)))
         return self._abs_cache[key]
 
     def Qinv(self, elems):
@@ -297,14 +336,16 @@ class ElasticDG:
                                               for e in elems])
         return self._qinv_cache[key]
 
-    def _neighbour_map(self, f):
-        """For face f of every element: flat index e2*Np + node2 of the matching
-        neighbour node per face node (-1 on tagged boundary faces)."""
-        if f in self._nbr_cache:
-            return self._nbr_cache[f]
+    def _neighbour_map(self, f, elems=None):
+        """For face f of each element in elems (default all): flat index e2*Np + node2
+        of the matching neighbour node per face node (-1 on tagged boundary faces)."""
+        elems = np.arange(self.nel) if elems is None else np.asarray(elems, dtype=np.int64)
+        key = (elems.tobytes(), f)
+        if key in self._nbr_cache:
+            return self._nbr_cache[key]
         N, n = self.N, self.N + 1
-        out = -np.ones((self.nel, n * n), dtype=np.int64)
-        for e in range(self.nel):
+        out = -np.ones((len(elems), n * n), dtype=np.int64)
+        for idx, e in enumerate(elems):
             e2 = self.etoe[e, f]
             if e2 < 0 or self.bc[e, f] != 0:
                 continue
@@ -313,15 +354,15 @@ class ElasticDG:
             for b in range(n):
                 for a in range(n):
                     a2, b2 = neighbour_face_position(o, a, b, N)
-                    out[e, a + n * b] = e2 * self.Np + fn2[a2 + n * b2]
-        self._nbr_cache[f] = out
+                    out[idx, a + n * b] = e2 * self.Np + fn2[a2 + n * b2]
+        self._nbr_cache[key] = out
         return out
 
     def exterior_state(self, u, elems, f):
         """(u^-, u^+) at the face nodes of face f of each element in elems: [9, ne, nf]."""
         fn = self.face_nodes[f]
         um = u[:, elems][:, :, fn]
-        nbr = self._neighbour_map(f)[elems]                   # [ne, nf]
+        nbr = self._neighbour_map(f, elems)                   # [ne, nf]
         tag = self.bc[elems, f]
         interior = (self.etoe[elems, f] >= 0) & (tag == 0)
         if np.any(~interior & (tag == 0)):
@@ -441,3 +482,13 @@ class ElasticDG:
 
     def c_max(self):
         return float(np.max(np.sqrt((self.lam + 2.0 * self.mu) / self.rho)))
+
+
+def h_min_corner_edges(x, N):
+    """Shortest element edge: the smallest distance between element corner nodes
+    joined by an element edge (12 per hexahedron)."""
+    n = N + 1
+    corners = [i + n * (j + n * k) for k in (0, N) for j in (0, N) for i in (0, N)]
+    xc = np.asarray(x)[:, corners, :]                       # [nel, 8, 3], corner c = (i, j, k) bits
+    edges = [(0, 1), (2, 3), (4, 5), (6, 7), (0, 2), (1, 3), (4, 6), (5, 7), (0, 4), (1, 5), (2, 6), (3, 7)]
+    return float(min(np.min(np.linalg.norm(xc[:, a] - xc[:, b], axis=-1)) for a, b in edges))

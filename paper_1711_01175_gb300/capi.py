@@ -1,0 +1,139 @@
+"""ctypes binding of libdgw.so (include/dgw.h), with the same names.
+
+Argument marshalling only: every numerical step runs in the library's CUDA
+kernels.  Loading fails loudly when the library has not been built -- there
+is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdgw.so")
+
+DGW_OK = 0
+STATUS = {0: "DGW_OK", -1: "DGW_ERR_ARG", -2: "DGW_ERR_STATE", -3: "DGW_ERR_OOM", -4: "DGW_ERR_CUDA",
+          -5: "DGW_ERR_UNSTABLE", -6: "DGW_ERR_TIMEOUT", -7: "DGW_ERR_UNSUPPORTED"}
+DGW_PRECISION_FP64 = 0
+DGW_PRECISION_MIXED = 1
+DGW_BC_INTERIOR, DGW_BC_FREE_SURFACE, DGW_BC_ABSORBING = 0, 1, 2
+
+
+class dgw_config(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("flux_tau", ctypes.c_int), ("precision", ctypes.c_int),
+                ("cfl", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+_D = ctypes.c_double
+_I = ctypes.c_int
+_I64 = ctypes.c_int64
+
+# name -> (restype, argtypes); exactly the functions declared in include/dgw.h
+SIGNATURES = {
+    "dgw_abi_version": (_I, []),
+    "dgw_reference_nodes": (_I, [_I, _P, _P]),
+    "dgw_create": (_I, [ctypes.POINTER(_P), _I, ctypes.POINTER(dgw_config)]),
+    "dgw_destroy": (_I, [_P]),
+    "dgw_mesh_upload": (_I, [_P, _I64, _P, _P, _P, _P, _P]),
+    "dgw_material_upload": (_I, [_P, _P, _P, _P]),
+    "dgw_rhs": (_I, [_P, _P, _P, _D, _P]),
+    "dgw_stage": (_I, [_P, _P, _P, _P, _I, _D, _D, _P]),
+    "dgw_step": (_I, [_P, _P, _P, _D, _D, _I, _P]),
+    "dgw_energy": (_I, [_P, _P, ctypes.POINTER(_D), _P]),
+    "dgw_adjoint_step": (_I, [_P, _P, _P, _P, _P, _D, _D, _I, _P]),
+    "dgw_dt_cfl": (_I, [_P, ctypes.POINTER(_D)]),
+    "dgw_last_error": (ctypes.c_char_p, [_P]),
+}
+
+_lib = None
+
+
+class DGWError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+def load(path: str = LIB_PATH):
+    """Load libdgw.so (built by ``paper_1711_01175_gb300.build.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build the CUDA library first "
+                           "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def check(status: int, ctx=None):
+    if status != DGW_OK:
+        msg = load().dgw_last_error(ctx).decode(errors="replace")
+        raise DGWError(status, msg)
+    return status
+
+
+# Thin wrappers with the C names (pointers are ints; see solver.py for tensors).
+def dgw_abi_version():
+    return load().dgw_abi_version()
+
+
+def dgw_reference_nodes(N, r_ptr, w_ptr):
+    return load().dgw_reference_nodes(N, r_ptr, w_ptr)
+
+
+def dgw_create(device, cfg):
+    h = _P()
+    st = load().dgw_create(ctypes.byref(h), device, ctypes.byref(cfg))
+    return st, h
+
+
+def dgw_destroy(ctx):
+    return load().dgw_destroy(ctx)
+
+
+def dgw_mesh_upload(ctx, nel, x, etoe, etof, orient, bc):
+    return load().dgw_mesh_upload(ctx, nel, x, etoe, etof, orient, bc)
+
+
+def dgw_material_upload(ctx, rho, lam, mu):
+    return load().dgw_material_upload(ctx, rho, lam, mu)
+
+
+def dgw_rhs(ctx, u, rhs, t, stream):
+    return load().dgw_rhs(ctx, u, rhs, t, stream)
+
+
+def dgw_stage(ctx, u_in, u_out, res, stage, t, dt, stream):
+    return load().dgw_stage(ctx, u_in, u_out, res, stage, t, dt, stream)
+
+
+def dgw_step(ctx, u, res, t0, dt, nsteps, stream):
+    return load().dgw_step(ctx, u, res, t0, dt, nsteps, stream)
+
+
+def dgw_energy(ctx, u, stream):
+    out = _D()
+    st = load().dgw_energy(ctx, u, ctypes.byref(out), stream)
+    return st, out.value
+
+
+def dgw_adjoint_step(ctx, lam_u, lam_res, grad_mat, u_ckpt, t0, dt, nsteps, stream):
+    return load().dgw_adjoint_step(ctx, lam_u, lam_res, grad_mat, u_ckpt, t0, dt, nsteps, stream)
+
+
+def dgw_dt_cfl(ctx):
+    out = _D()
+    st = load().dgw_dt_cfl(ctx, ctypes.byref(out))
+    return st, out.value
+
+
+def dgw_last_error(ctx):
+    return load().dgw_last_error(ctx).decode(errors="replace")

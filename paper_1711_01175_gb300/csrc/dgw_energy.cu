@@ -1,0 +1,71 @@
+// Discrete energy E = 1/2 sum_K sum_nodes w J u^T Q u, Q = diag(rho I, C_V^{-1}).
+//
+// The isotropic compliance in Voigt form gives
+//   sigma^T C_V^{-1} sigma = (1/(2 mu)) [sum_i s_ii^2 - lam/(3 lam + 2 mu) (tr s)^2]
+//                            + (1/mu) (s23^2 + s13^2 + s12^2),
+// the energy of the local solvers' energy identities (the paper's Section 4
+// proofs use the same quadratic form with the time weight).  FP64 throughout;
+// fixed grid and fixed reduction order, so the value is bit-reproducible.
+#include "dgw_internal.cuh"
+
+namespace dgw {
+
+namespace {
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (warp == 0) {
+    s = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  }
+  return s;   // valid in thread 0
+}
+
+__global__ void __launch_bounds__(kEnergyThreads)
+energy_partial_kernel(const double* __restrict__ u, const double* __restrict__ wJ,
+                      const double* __restrict__ ec, long long nel, int Np, double* partials) {
+  __shared__ double red[32];
+  const size_t total = (size_t)nel * Np;
+  double acc = 0.0;
+  for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total;
+       g += (size_t)gridDim.x * blockDim.x) {
+    const long long e = (long long)(g / Np);
+    const double rho = ec[e], i2mu = ec[nel + e], lfac = ec[2 * nel + e], imu = ec[3 * nel + e];
+    const double v1 = u[g], v2 = u[total + g], v3 = u[2 * total + g];
+    const double s1 = u[3 * total + g], s2 = u[4 * total + g], s3 = u[5 * total + g];
+    const double s4 = u[6 * total + g], s5 = u[7 * total + g], s6 = u[8 * total + g];
+    const double tr = s1 + s2 + s3;
+    const double kin = rho * (v1 * v1 + v2 * v2 + v3 * v3);
+    const double pot = i2mu * (s1 * s1 + s2 * s2 + s3 * s3 - lfac * tr * tr) +
+                       imu * (s4 * s4 + s5 * s5 + s6 * s6);
+    acc += wJ[g] * (kin + pot);
+  }
+  const double s = block_sum(acc, red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(kEnergyThreads)
+energy_final_kernel(const double* __restrict__ partials, int nparts, double* result) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += partials[i];
+  const double s = block_sum(acc, red);
+  if (threadIdx.x == 0) *result = 0.5 * s;
+}
+
+}  // namespace
+
+cudaError_t launch_energy(const double* u, const double* wJ, const double* ec, long long nel, int Np,
+                          double* partials, double* result, cudaStream_t s) {
+  energy_partial_kernel<<<kEnergyBlocks, kEnergyThreads, 0, s>>>(u, wJ, ec, nel, Np, partials);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  energy_final_kernel<<<1, kEnergyThreads, 0, s>>>(partials, kEnergyBlocks, result);
+  return cudaGetLastError();
+}
+
+}  // namespace dgw

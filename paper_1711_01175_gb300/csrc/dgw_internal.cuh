@@ -1,0 +1,105 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "dgw.h"
+
+namespace dgw {
+
+constexpr int kMaxN = 7;
+constexpr int kFields = 9;
+
+// Reference element on the host: GLL nodes/weights and the 1-D derivative
+// matrix D[i*(N+1)+j] = l_j'(r_i).
+struct RefElem {
+  int N = 0;
+  double r[kMaxN + 1] = {};
+  double w[kMaxN + 1] = {};
+  double D[(kMaxN + 1) * (kMaxN + 1)] = {};
+};
+bool build_ref_elem(int N, RefElem* out);
+
+// Elements per CTA and threads per CTA of the fused stage kernel, per degree.
+template <int N>
+struct Shape {
+  static constexpr int n = N + 1;
+  static constexpr int Np = n * n * n;
+  static constexpr int nf = n * n;
+  static constexpr int EPB = (N == 1) ? 16 : (N == 2) ? 9 : (N == 3) ? 4 : (N == 4) ? 2 : 1;
+  static constexpr int NTILE = EPB * Np;
+  static constexpr int NT = ((NTILE + 31) / 32) * 32;
+  static constexpr int NFACE_ITEMS = EPB * 6 * nf;
+};
+
+// Neighbour-map sentinels for boundary faces (the map holds e*Np + node otherwise).
+constexpr int kGhostFreeSurface = -1;
+constexpr int kGhostAbsorbing = -2;
+
+// Arguments of one fused stage launch.  Real is double (FP64 path) or float
+// (mixed path) for the geometry, face and material arrays.
+struct StageParams {
+  const double* u_in;     // [9][nel][Np]
+  double* out;            // rhs (rhs mode) or u_out (LSRK mode), [9][nel][Np]
+  double* res;            // LSRK register [9][nel][Np] (LSRK mode only)
+  const void* geo;        // Real [10][nel][Np]: Ja^i_k at 3*i+k, then 1/J
+  const void* face;       // Real [12][nel][6*nf]: P (xx,yy,zz,yz,xz,xy), then P^{-1}
+  const int* vmapP;       // [nel][6*nf]: neighbour flat node index or ghost sentinel
+  const void* mat;        // Real [3][nel]: 1/rho, lambda, mu
+  long long nel;
+  double a, b, dt;        // LSRK coefficients of this stage and the step size
+  double tau;             // 0 central, 1 upwind
+  double w_end_inv;       // 1 / w_0 (GLL end weight)
+  double D[(kMaxN + 1) * (kMaxN + 1)];
+};
+
+// Launchers implemented in dgw_stage_fp64.cu / dgw_stage_mixed.cu.
+cudaError_t launch_stage_fp64(int N, bool lsrk, const StageParams& p, cudaStream_t s);
+cudaError_t launch_stage_mixed(int N, bool lsrk, const StageParams& p, cudaStream_t s);
+void stage_shape(int N, int* epb, int* threads);
+
+// Geometry (dgw_geometry.cu).
+struct GeometryOut {
+  double* geo;       // [10][nel][Np]  Ja (9) then 1/J
+  double* face;      // [12][nel][6*nf] P then P^{-1}
+  double* wJ;        // [nel][Np]       w_i w_j w_k J
+  double* minJ;      // [nel]
+};
+cudaError_t launch_geometry(int N, const double* x, long long nel, const double* D, const double* w,
+                            const GeometryOut& out, cudaStream_t s);
+cudaError_t launch_to_float(const double* src, float* dst, size_t n, cudaStream_t s);
+
+// Energy (dgw_energy.cu): partial sums per block, then one final block.
+constexpr int kEnergyBlocks = 152 * 4;
+constexpr int kEnergyThreads = 256;
+cudaError_t launch_energy(const double* u, const double* wJ, const double* ec, long long nel, int Np,
+                          double* partials, double* result, cudaStream_t s);
+
+}  // namespace dgw
+
+struct dgw_ctx {
+  int device = 0;
+  dgw_config cfg{};
+  dgw::RefElem ref;
+  long long nel = 0;
+  bool has_mesh = false;
+  bool has_material = false;
+  // device memory owned by the context
+  void* geo = nullptr;       // Real [10][nel][Np]
+  void* face = nullptr;      // Real [12][nel][6*nf]
+  int* vmapP = nullptr;      // [nel][6*nf]
+  void* mat = nullptr;       // Real [3][nel]
+  double* ec = nullptr;      // [4][nel] energy constants: rho, 1/(2 mu), lam/(3 lam + 2 mu), 1/mu
+  double* wJ = nullptr;      // [nel][Np]
+  double* u2 = nullptr;      // second state buffer for the stage ping-pong
+  double* partials = nullptr;  // energy partial sums + result slot
+  double* stage_u = nullptr;   // host-pointer staging buffers
+  double* stage_res = nullptr;
+  double* pinned = nullptr;    // pinned host slot for the energy value
+  double h_min = 0.0;
+  double c_max = 0.0;
+  std::string err;
+};

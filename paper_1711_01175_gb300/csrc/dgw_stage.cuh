@@ -1,0 +1,313 @@
+// Fused DG stage kernel: split-form volume term, face gather + upwind flux,
+// diagonal GLL lift, Q^{-1}, and (optionally) the 2N-storage Runge-Kutta update.
+//
+// One CTA holds EPB elements; thread t owns node t % Np of element t / Np.
+//   1. u of the tile (FP64 in HBM) -> shared memory in Real.
+//   2. Volume term per direction i (eq. LPDE in curvilinear split form):
+//        acc += D_i (A(Ja^i) u)   [conservative part; A(Ja^i)u staged in smem]
+//        acc += A(Ja^i) (D_i u)   [non-conservative part]
+//      and vol = -1/2 * (1/J) * acc.  A(m)u = -(sigma m, Voigt(sym(m (x) v))).
+//   3. Face items (EPB*6*nf of them, spread over all threads): own trace from
+//      smem, neighbour trace from HBM/L2 through the neighbour map (or the
+//      boundary ghost), flux difference 1/2 (A(m) - tau |A(m)|)(u^- - u^+) with
+//      m = n sJ the scaled outward normal and |A(m)| = diag(P, B P^{-1} B^T),
+//      P = (B^T B)^{1/2} -- the upwind HDG flux of eq. RiemannFluxBoth with the
+//      trace eliminated by eq. HDGeqn/iHDGtrace -- scaled by the lift factor
+//      (1/J)/w_0 and staged in smem.
+//   4. Each node adds the lifted flux of the faces it lies on, applies
+//      Q^{-1} = diag(1/rho, C_V), then writes rhs or performs
+//      res <- a res + dt rhs, u_out <- u_in + b res in FP64.
+#pragma once
+
+#include <type_traits>
+
+#include "dgw_internal.cuh"
+
+namespace dgw {
+
+// out = A_+(m) w with A(m) = -A_+(m):  (sigma m, Voigt(sym(m (x) v))).
+template <typename Real>
+__device__ __forceinline__ void apply_Apos(Real m1, Real m2, Real m3, const Real* w, Real* out) {
+  out[0] = m1 * w[3] + m2 * w[8] + m3 * w[7];
+  out[1] = m1 * w[8] + m2 * w[4] + m3 * w[6];
+  out[2] = m1 * w[7] + m2 * w[6] + m3 * w[5];
+  out[3] = m1 * w[0];
+  out[4] = m2 * w[1];
+  out[5] = m3 * w[2];
+  out[6] = m2 * w[2] + m3 * w[1];
+  out[7] = m1 * w[2] + m3 * w[0];
+  out[8] = m1 * w[1] + m2 * w[0];
+}
+
+template <int N, typename Real, bool LSRK>
+__global__ void __launch_bounds__(Shape<N>::NT) stage_kernel(const StageParams p) {
+  using S = Shape<N>;
+  constexpr int n = S::n, Np = S::Np, nf = S::nf, EPB = S::EPB, NT = S::NT;
+  constexpr int NTILE = S::NTILE, NFI = S::NFACE_ITEMS;
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* u_s = reinterpret_cast<Real*>(smem_raw);   // [9][NTILE]
+  Real* f_s = u_s + 9 * NTILE;                      // [10][NTILE]: flux, later Ja + 1/J
+  Real* x_s = f_s + 10 * NTILE;                     // [9][NFI]: lifted face flux
+  Real* D_s = x_s + 9 * NFI;                        // [n*n]
+
+  const int t = threadIdx.x;
+  for (int i = t; i < n * n; i += NT) D_s[i] = static_cast<Real>(p.D[i]);
+
+  const long long e0 = static_cast<long long>(blockIdx.x) * EPB;
+  const int el = t / Np;
+  const int node = t - el * Np;
+  const long long e = e0 + el;
+  const bool in_tile = t < NTILE;
+  const bool active = in_tile && (e < p.nel);
+  const size_t fstride = static_cast<size_t>(p.nel) * Np;
+  const size_t gidx = active ? static_cast<size_t>(e) * Np + node : 0;
+  const Real* geo = static_cast<const Real*>(p.geo);
+
+  double u_keep[LSRK && !std::is_same<Real, double>::value ? 9 : 1];
+  Real ja[9];
+  Real jinv = 0;
+  if (active) {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      const double v = p.u_in[q * fstride + gidx];
+      if constexpr (LSRK && !std::is_same<Real, double>::value) u_keep[q] = v;
+      u_s[q * NTILE + t] = static_cast<Real>(v);
+    }
+#pragma unroll
+    for (int c = 0; c < 9; ++c) ja[c] = geo[c * fstride + gidx];
+    jinv = geo[9 * fstride + gidx];
+  } else {
+#pragma unroll
+    for (int c = 0; c < 9; ++c) ja[c] = 0;
+    if (in_tile) {
+#pragma unroll
+      for (int q = 0; q < 9; ++q) u_s[q * NTILE + t] = 0;
+    }
+  }
+  __syncthreads();
+
+  const int ix = node % n;
+  const int iy = (node / n) % n;
+  const int iz = node / nf;
+
+  Real acc[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) acc[q] = 0;
+
+#pragma unroll
+  for (int dir = 0; dir < 3; ++dir) {
+    const Real m1 = ja[3 * dir + 0], m2 = ja[3 * dir + 1], m3 = ja[3 * dir + 2];
+    if (in_tile) {
+      Real w[9], F[9];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) w[q] = u_s[q * NTILE + t];
+      apply_Apos(m1, m2, m3, w, F);
+#pragma unroll
+      for (int q = 0; q < 9; ++q) f_s[q * NTILE + t] = F[q];
+    }
+    __syncthreads();
+    if (in_tile) {
+      const int stride = dir == 0 ? 1 : (dir == 1 ? n : nf);
+      const int a = dir == 0 ? ix : (dir == 1 ? iy : iz);
+      const int base = t - a * stride;
+      Real Drow[n];
+#pragma unroll
+      for (int b = 0; b < n; ++b) Drow[b] = D_s[a * n + b];
+      Real du[9];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) {
+        Real cs = 0, ds = 0;
+#pragma unroll
+        for (int b = 0; b < n; ++b) {
+          cs += Drow[b] * f_s[q * NTILE + base + b * stride];
+          ds += Drow[b] * u_s[q * NTILE + base + b * stride];
+        }
+        acc[q] += cs;
+        du[q] = ds;
+      }
+      Real G[9];
+      apply_Apos(m1, m2, m3, du, G);
+#pragma unroll
+      for (int q = 0; q < 9; ++q) acc[q] += G[q];
+    }
+    __syncthreads();
+  }
+
+  // Stage the geometry of every node for the face items.
+  if (in_tile) {
+#pragma unroll
+    for (int c = 0; c < 9; ++c) f_s[c * NTILE + t] = ja[c];
+    f_s[9 * NTILE + t] = jinv;
+  }
+  __syncthreads();
+
+  // Face items: lifted flux differences.
+  {
+    const Real* face = static_cast<const Real*>(p.face);
+    const size_t ffstride = static_cast<size_t>(p.nel) * 6 * nf;
+    const Real tau = static_cast<Real>(p.tau);
+    const Real half_lift = static_cast<Real>(0.5 * p.w_end_inv);
+    for (int it = t; it < NFI; it += NT) {
+      const int eli = it / (6 * nf);
+      const int r = it - eli * (6 * nf);
+      const long long ei = e0 + eli;
+      if (ei >= p.nel) continue;
+      const int f = r / nf;
+      const int pf = r - f * nf;
+      const int d = f >> 1;
+      const bool hi = (f & 1) != 0;
+      const int fa = pf % n, fb = pf / n;
+      const int cd = hi ? N : 0;
+      const int c0 = d == 0 ? cd : fa;
+      const int c1 = d == 0 ? fa : (d == 1 ? cd : fb);
+      const int c2 = d == 2 ? cd : fb;
+      const int vn = c0 + n * (c1 + n * c2);
+      const int sidx = eli * Np + vn;
+
+      Real du[9];
+      const int g = p.vmapP[static_cast<size_t>(ei) * 6 * nf + r];
+      if (g >= 0) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q)
+          du[q] = u_s[q * NTILE + sidx] - static_cast<Real>(p.u_in[q * fstride + g]);
+      } else if (g == kGhostFreeSurface) {
+        // exterior (v, -sigma): jump (0, 2 sigma)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) du[q] = 0;
+#pragma unroll
+        for (int q = 3; q < 9; ++q) du[q] = 2 * u_s[q * NTILE + sidx];
+      } else {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) du[q] = u_s[q * NTILE + sidx];
+      }
+      const Real sgn = hi ? Real(1) : Real(-1);
+      const Real m1 = sgn * f_s[(3 * d + 0) * NTILE + sidx];
+      const Real m2 = sgn * f_s[(3 * d + 1) * NTILE + sidx];
+      const Real m3 = sgn * f_s[(3 * d + 2) * NTILE + sidx];
+      const Real jv = f_s[9 * NTILE + sidx];
+
+      Real Ad[9];
+      apply_Apos(m1, m2, m3, du, Ad);      // A_+(m) du = -A(m) du
+      Real flux[9];
+      if (tau != Real(0)) {
+        const size_t fi = static_cast<size_t>(ei) * 6 * nf + r;
+        Real P[6], Pi[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+          P[c] = face[c * ffstride + fi];
+          Pi[c] = face[(6 + c) * ffstride + fi];
+        }
+        // |A(m)| du = (P dv, B P^{-1} B^T dsigma); B^T dsigma = dsigma m = Ad[0..2]
+        const Real pv0 = P[0] * du[0] + P[5] * du[1] + P[4] * du[2];
+        const Real pv1 = P[5] * du[0] + P[1] * du[1] + P[3] * du[2];
+        const Real pv2 = P[4] * du[0] + P[3] * du[1] + P[2] * du[2];
+        const Real z0 = Pi[0] * Ad[0] + Pi[5] * Ad[1] + Pi[4] * Ad[2];
+        const Real z1 = Pi[5] * Ad[0] + Pi[1] * Ad[1] + Pi[3] * Ad[2];
+        const Real z2 = Pi[4] * Ad[0] + Pi[3] * Ad[1] + Pi[2] * Ad[2];
+        const Real absd[9] = {pv0, pv1, pv2, m1 * z0, m2 * z1, m3 * z2,
+                              m2 * z2 + m3 * z1, m1 * z2 + m3 * z0, m1 * z1 + m2 * z0};
+        // 1/2 (A(m) - tau|A(m)|) du * (1/J)/w_0 = -1/2 (A_+ du + tau |A| du) (1/J)/w_0
+        const Real s = -half_lift * jv;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) flux[q] = s * (Ad[q] + tau * absd[q]);
+      } else {
+        const Real s = -half_lift * jv;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) flux[q] = s * Ad[q];
+      }
+#pragma unroll
+      for (int q = 0; q < 9; ++q) x_s[q * NFI + it] = flux[q];
+    }
+  }
+  __syncthreads();
+
+  if (!active) return;
+
+  // vol = -1/2 (1/J) (-acc_+) = +1/2 (1/J) acc_+  (acc holds A_+ terms)
+  Real r[9];
+  const Real hv = static_cast<Real>(0.5) * jinv;
+#pragma unroll
+  for (int q = 0; q < 9; ++q) r[q] = hv * acc[q];
+  const int fb0 = el * 6 * nf;
+  auto add_face = [&](int f, int pidx) {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) r[q] += x_s[q * NFI + fb0 + f * nf + pidx];
+  };
+  if (ix == 0) add_face(0, iy + n * iz);
+  if (ix == N) add_face(1, iy + n * iz);
+  if (iy == 0) add_face(2, ix + n * iz);
+  if (iy == N) add_face(3, ix + n * iz);
+  if (iz == 0) add_face(4, ix + n * iy);
+  if (iz == N) add_face(5, ix + n * iy);
+
+  // Q^{-1}: velocity rows / rho, stress rows by the isotropic stiffness C_V.
+  const Real* mat = static_cast<const Real*>(p.mat);
+  const Real irho = mat[e];
+  const Real lam = mat[p.nel + e];
+  const Real mu = mat[2 * p.nel + e];
+  double rhs[9];
+  rhs[0] = static_cast<double>(irho * r[0]);
+  rhs[1] = static_cast<double>(irho * r[1]);
+  rhs[2] = static_cast<double>(irho * r[2]);
+  const Real tr = r[3] + r[4] + r[5];
+  const Real two_mu = mu + mu;
+  rhs[3] = static_cast<double>(lam * tr + two_mu * r[3]);
+  rhs[4] = static_cast<double>(lam * tr + two_mu * r[4]);
+  rhs[5] = static_cast<double>(lam * tr + two_mu * r[5]);
+  rhs[6] = static_cast<double>(mu * r[6]);
+  rhs[7] = static_cast<double>(mu * r[7]);
+  rhs[8] = static_cast<double>(mu * r[8]);
+
+  if constexpr (!LSRK) {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) p.out[q * fstride + gidx] = rhs[q];
+  } else {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      double uq;
+      if constexpr (std::is_same<Real, double>::value) {
+        uq = u_s[q * NTILE + t];
+      } else {
+        uq = u_keep[q];
+      }
+      const double rn = p.a * p.res[q * fstride + gidx] + p.dt * rhs[q];
+      p.res[q * fstride + gidx] = rn;
+      p.out[q * fstride + gidx] = uq + p.b * rn;
+    }
+  }
+}
+
+template <int N, typename Real, bool LSRK>
+cudaError_t launch_stage_t(const StageParams& p, cudaStream_t s) {
+  using S = Shape<N>;
+  const size_t smem = sizeof(Real) * (9 * S::NTILE + 10 * S::NTILE + 9 * S::NFACE_ITEMS + S::n * S::n);
+  cudaError_t err = cudaFuncSetAttribute(stage_kernel<N, Real, LSRK>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  const long long blocks = (p.nel + S::EPB - 1) / S::EPB;
+  if (blocks <= 0) return cudaSuccess;
+  stage_kernel<N, Real, LSRK><<<(unsigned)blocks, S::NT, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t launch_stage_any(int N, bool lsrk, const StageParams& p, cudaStream_t s) {
+#define DGW_CASE(NN)                                                                   \
+  case NN:                                                                             \
+    return lsrk ? launch_stage_t<NN, Real, true>(p, s) : launch_stage_t<NN, Real, false>(p, s);
+  switch (N) {
+    DGW_CASE(1)
+    DGW_CASE(2)
+    DGW_CASE(3)
+    DGW_CASE(4)
+    DGW_CASE(5)
+    DGW_CASE(6)
+    DGW_CASE(7)
+    default:
+      return cudaErrorInvalidValue;
+  }
+#undef DGW_CASE
+}
+
+}  // namespace dgw

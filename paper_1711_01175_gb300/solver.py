@@ -1,0 +1,126 @@
+"""Tensor-level front end over the C ABI: one ``Solver`` per mesh and medium.
+
+Field tensors are ``[9, nel, Np]`` float64, either CUDA tensors (device
+pointers; the work is enqueued on torch's current stream) or CPU tensors /
+numpy arrays (host pointers; the library stages them through its own device
+buffers).  PyTorch only provides device memory and streams here.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import capi
+
+
+def _stream_handle(stream=None):
+    import torch
+    if stream is None:
+        if not torch.cuda.is_available():
+            return None
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(a):
+    """Raw pointer of a contiguous torch tensor or numpy array."""
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return ctypes.c_void_p(a.ctypes.data)
+    if not a.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ctypes.c_void_p(a.data_ptr())
+
+
+def reference_nodes(N: int):
+    """GLL nodes and weights the library uses (numpy float64, length N+1)."""
+    r = np.zeros(N + 1)
+    w = np.zeros(N + 1)
+    capi.check(capi.dgw_reference_nodes(N, _ptr(r), _ptr(w)))
+    return r, w
+
+
+class Solver:
+    """A DG elastic-wave operator on one mesh/medium (owns a dgw_ctx)."""
+
+    def __init__(self, N: int, tau: int = 1, precision: str = "fp64", cfl: float = 0.5, device: int = 0):
+        prec = {"fp64": capi.DGW_PRECISION_FP64, "mixed": capi.DGW_PRECISION_MIXED}[precision]
+        self.N, self.tau, self.precision = int(N), int(tau), precision
+        self.Np = (self.N + 1) ** 3
+        cfg = capi.dgw_config(self.N, self.tau, prec, float(cfl))
+        st, h = capi.dgw_create(int(device), cfg)
+        capi.check(st)
+        self._ctx = h
+        self.nel = 0
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            capi.dgw_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        return capi.check(st, self._ctx)
+
+    def upload_mesh(self, x, etoe, etof, orient, bc):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        nel = x.shape[0]
+        if x.shape != (nel, self.Np, 3):
+            raise ValueError(f"x must be [nel, {self.Np}, 3]")
+        arrs = [np.ascontiguousarray(etoe, dtype=np.int64), np.ascontiguousarray(etof, dtype=np.int8),
+                np.ascontiguousarray(orient, dtype=np.int8), np.ascontiguousarray(bc, dtype=np.int8)]
+        for a in arrs:
+            if a.shape != (nel, 6):
+                raise ValueError("connectivity arrays must be [nel, 6]")
+        self._check(capi.dgw_mesh_upload(self._ctx, nel, _ptr(x), *[_ptr(a) for a in arrs]))
+        self.nel = nel
+
+    def upload_material(self, rho, lam, mu):
+        arrs = [np.ascontiguousarray(v, dtype=np.float64) for v in (rho, lam, mu)]
+        for a in arrs:
+            if a.shape != (self.nel,):
+                raise ValueError("material arrays must be [nel]")
+        self._check(capi.dgw_material_upload(self._ctx, *[_ptr(a) for a in arrs]))
+
+    def _field_check(self, a, name):
+        shape = tuple(a.shape)
+        if shape != (9, self.nel, self.Np):
+            raise ValueError(f"{name} must be [9, {self.nel}, {self.Np}], got {shape}")
+        if str(a.dtype) not in ("float64", "torch.float64"):
+            raise ValueError(f"{name} must be float64")
+
+    def rhs(self, u, out, t: float = 0.0, stream=None):
+        self._field_check(u, "u")
+        self._field_check(out, "out")
+        self._check(capi.dgw_rhs(self._ctx, _ptr(u), _ptr(out), float(t), _stream_handle(stream)))
+        return out
+
+    def stage(self, u_in, u_out, res, s: int, dt: float, t: float = 0.0, stream=None):
+        for a, nm in ((u_in, "u_in"), (u_out, "u_out"), (res, "res")):
+            self._field_check(a, nm)
+        self._check(capi.dgw_stage(self._ctx, _ptr(u_in), _ptr(u_out), _ptr(res), int(s), float(t),
+                                   float(dt), _stream_handle(stream)))
+
+    def step(self, u, res, dt: float, nsteps: int = 1, t0: float = 0.0, stream=None):
+        self._field_check(u, "u")
+        self._field_check(res, "res")
+        self._check(capi.dgw_step(self._ctx, _ptr(u), _ptr(res), float(t0), float(dt), int(nsteps),
+                                  _stream_handle(stream)))
+
+    def energy(self, u, stream=None) -> float:
+        self._field_check(u, "u")
+        st, val = capi.dgw_energy(self._ctx, _ptr(u), _stream_handle(stream))
+        self._check(st)
+        return val
+
+    def dt_cfl(self) -> float:
+        st, val = capi.dgw_dt_cfl(self._ctx)
+        self._check(st)
+        return val

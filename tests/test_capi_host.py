@@ -1,0 +1,82 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds, loads,
+exports every function include/dgw.h declares, and its host-only calls work."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1711_01175_gb300 import build, capi
+    build.build()
+    return capi.load()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "dgw.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(dgw_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("dgw_mesh_upload", "dgw_material_upload", "dgw_rhs", "dgw_step", "dgw_energy",
+                     "dgw_adjoint_step", "dgw_create", "dgw_destroy"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_1711_01175_gb300 import capi
+    names = declared_functions()
+    for name in names:
+        assert hasattr(lib, name), name
+    assert sorted(capi.SIGNATURES) == names
+
+
+def test_abi_version(lib):
+    text = open(os.path.join(ROOT, "include", "dgw.h")).read()
+    v = int(re.search(r"#define DGW_ABI_VERSION (\d+)", text).group(1))
+    assert lib.dgw_abi_version() == v
+
+
+@pytest.mark.parametrize("N", range(1, 8))
+def test_reference_nodes_match_oracle_gll(lib, N):
+    from paper_1711_01175_gb300 import reference_nodes
+    r, w = reference_nodes(N)
+    ro, wo = oracle.gll(N)
+    np.testing.assert_allclose(r, ro, atol=2e-16 * 4)
+    np.testing.assert_allclose(w, wo, rtol=1e-14)
+
+
+def test_reference_nodes_rejects_bad_degree(lib):
+    from paper_1711_01175_gb300 import capi
+    r = np.zeros(10)
+    w = np.zeros(10)
+    for N in (0, 8, -1):
+        st = lib.dgw_reference_nodes(N, r.ctypes.data, w.ctypes.data)
+        assert st == -1
+        assert "outside" in capi.dgw_last_error(None)
+    assert lib.dgw_reference_nodes(3, None, None) == -1
+
+
+def test_create_rejects_bad_config_without_touching_a_device(lib):
+    from paper_1711_01175_gb300 import capi
+    for cfg in (capi.dgw_config(0, 1, 0, 0.5), capi.dgw_config(3, 2, 0, 0.5),
+                capi.dgw_config(3, 1, 5, 0.5), capi.dgw_config(3, 1, 0, -1.0)):
+        st, h = capi.dgw_create(0, cfg)
+        assert st == -1 and not h.value
+
+
+def test_calls_on_null_context_fail_cleanly(lib):
+    from paper_1711_01175_gb300 import capi
+    assert capi.dgw_rhs(None, None, None, 0.0, None) == -1
+    assert capi.dgw_step(None, None, None, 0.0, 0.1, 1, None) == -1
+    assert capi.dgw_mesh_upload(None, 1, None, None, None, None, None) == -1
+    assert capi.dgw_destroy(None) == 0

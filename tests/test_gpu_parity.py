@@ -1,0 +1,256 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+FP64 path bar: relative L2 <= 1e-12 per right-hand side and per stage.
+Mixed path bar: stated FP32-level bound (see MIXED_RHS_TOL).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+from harness import Case, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+# FP32 volume/flux arithmetic on FP32 geometry: unit round-off 6e-8 times the
+# O(N^2) amplification of the derivative and lift operators on rough data.
+MIXED_RHS_TOL = 2e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__ as g
+    g.build()
+
+
+def torch_cuda(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+# ------------------------------------------------------------------ rhs parity
+def test_rhs_parity_workload_plane_wave():
+    cfg = wl.parity_config()
+    c = Case(cfg.E, cfg.N, cfg.amplitude, cfg.periodic, initial="plane_p_wave")
+    assert rel_l2(c.gpu_rhs(c.u0), c.op.rhs(c.u0)) < FP64_TOL
+
+
+@pytest.mark.parametrize("N", range(1, 8))
+def test_rhs_parity_every_degree_rotated_ragged(N):
+    """27 elements (ragged last CTA for EPB > 1), all eight face permutation codes,
+    free surface + absorbing boundaries, heterogeneous medium."""
+    c = Case(3, N, 0.1, periodic=(True, False, False),
+             boundary={2: wl.BC_FREE_SURFACE, 3: wl.BC_ABSORBING, 4: wl.BC_ABSORBING, 5: wl.BC_FREE_SURFACE},
+             material=N, rotate=100 + N, seed=N)
+    assert rel_l2(c.gpu_rhs(c.u0), c.op.rhs(c.u0)) < FP64_TOL
+
+
+def test_rhs_parity_single_self_periodic_element():
+    c = Case(1, 4, 0.08, seed=3)
+    assert rel_l2(c.gpu_rhs(c.u0), c.op.rhs(c.u0)) < FP64_TOL
+
+
+@pytest.mark.parametrize("tau", [0, 1])
+def test_rhs_parity_flux_choice(tau):
+    c = Case(3, 3, 0.1, material=7, tau=tau, seed=4)
+    assert rel_l2(c.gpu_rhs(c.u0), c.op.rhs(c.u0)) < FP64_TOL
+
+
+def test_rhs_parity_large_cut():
+    """16^3 cut of the large workload recipe: N=4, Morton order, warp 0.1, smooth
+    random medium, z=0 absorbing, z=1 free surface."""
+    cfg = wl.large_config(E=16)
+    c = Case(cfg.E, cfg.N, cfg.amplitude, cfg.periodic, cfg.boundary, cfg.order, material=1,
+             initial="gaussian_pulse")
+    assert rel_l2(c.gpu_rhs(c.u0), c.op.rhs(c.u0)) < FP64_TOL
+    u = wl.random_state(c.mesh.nel, 125, 9)
+    assert rel_l2(c.gpu_rhs(u), c.op.rhs(u)) < FP64_TOL
+
+
+# ---------------------------------------------------------------- stage parity
+def _stages(c, dt):
+    """Run one LSRK step stage by stage on both sides; compare after each stage."""
+    import torch
+    u = torch_cuda(c.u0)
+    u_next = torch.empty_like(u)
+    res = torch.zeros_like(u)
+    uo, ro = c.u0.copy(), np.zeros_like(c.u0)
+    worst = 0.0
+    for s in range(5):
+        c.solver.stage(u, u_next, res, s, dt)
+        uo, ro = c.op.lsrk_stage(uo, ro, s, dt)
+        worst = max(worst, rel_l2(u_next.cpu().numpy(), uo), rel_l2(res.cpu().numpy(), ro))
+        u, u_next = u_next, u
+    return worst
+
+
+def test_stage_parity_workload():
+    cfg = wl.parity_config()
+    c = Case(cfg.E, cfg.N, cfg.amplitude, cfg.periodic, initial="plane_p_wave")
+    dt = c.solver.dt_cfl()
+    assert _stages(c, dt) < FP64_TOL
+
+
+def test_stage_parity_large_cut():
+    cfg = wl.large_config(E=12)
+    c = Case(cfg.E, cfg.N, cfg.amplitude, cfg.periodic, cfg.boundary, cfg.order, material=1,
+             initial="gaussian_pulse")
+    assert _stages(c, c.solver.dt_cfl()) < FP64_TOL
+
+
+def test_parity_workload_100_steps():
+    """The full parity workload: 4^3, N=3, CFL 0.5, 100 LSRK steps."""
+    import torch
+    cfg = wl.parity_config()
+    c = Case(cfg.E, cfg.N, cfg.amplitude, cfg.periodic, initial="plane_p_wave")
+    dt = c.solver.dt_cfl()
+    dt_or = oracle.cfl_dt(cfg.cfl, oracle.h_min_corner_edges(c.x_or, cfg.N), c.op.c_max(), cfg.N)
+    assert abs(dt - dt_or) <= 1e-15 * dt_or
+    u = torch_cuda(c.u0)
+    res = torch.zeros_like(u)
+    c.solver.step(u, res, dt, cfg.steps)
+    uo, ro = c.u0.copy(), np.zeros_like(c.u0)
+    for _ in range(cfg.steps):
+        uo, ro = c.op.step(uo, ro, dt)
+    assert rel_l2(u.cpu().numpy(), uo) < FP64_TOL
+    assert rel_l2(res.cpu().numpy(), ro) < 1e-11
+
+
+# ---------------------------------------------------------------------- energy
+def test_energy_parity_and_decay():
+    import torch
+    cfg = wl.large_config(E=8)
+    c = Case(cfg.E, cfg.N, cfg.amplitude, cfg.periodic, cfg.boundary, cfg.order, material=1,
+             initial="gaussian_pulse")
+    u = torch_cuda(c.u0)
+    e_gpu = c.solver.energy(u)
+    e_or = c.op.energy(c.u0)
+    assert abs(e_gpu - e_or) <= 1e-13 * e_or
+    assert c.solver.energy(u) == e_gpu            # fixed reduction order: bit-reproducible
+    res = torch.zeros_like(u)
+    dt = c.solver.dt_cfl()
+    prev = e_gpu
+    for _ in range(10):
+        c.solver.step(u, res, dt, 2)
+        e = c.solver.energy(u)
+        assert e <= prev * (1 + 1e-13)
+        prev = e
+
+
+def test_host_pointer_paths_match_device_paths():
+    import torch
+    c = Case(3, 4, 0.1, material=2, seed=8)
+    dt = c.solver.dt_cfl()
+    u_h = c.u0.copy()
+    r_h = np.zeros_like(u_h)
+    c.solver.step(u_h, r_h, dt, 2)
+    u_d = torch_cuda(c.u0)
+    r_d = torch.zeros_like(u_d)
+    c.solver.step(u_d, r_d, dt, 2)
+    assert np.array_equal(u_h, u_d.cpu().numpy())
+    assert np.array_equal(r_h, r_d.cpu().numpy())
+    out_h = np.empty_like(u_h)
+    c.solver.rhs(c.u0, out_h)
+    assert np.array_equal(out_h, c.gpu_rhs(c.u0))
+    assert c.solver.energy(u_h) == c.solver.energy(u_d)
+
+
+# -------------------------------------------------------------- mixed precision
+def test_mixed_precision_rhs_bound():
+    cfg = wl.large_config(E=8)
+    for initial in ("gaussian_pulse", "random"):
+        c = Case(cfg.E, cfg.N, cfg.amplitude, cfg.periodic, cfg.boundary, cfg.order, material=1,
+                 initial=initial, precision="mixed")
+        err = rel_l2(c.gpu_rhs(c.u0), c.op.rhs(c.u0))
+        assert err < MIXED_RHS_TOL, err
+
+
+def test_mixed_precision_step_bound():
+    import torch
+    cfg = wl.parity_config()
+    c = Case(cfg.E, cfg.N, cfg.amplitude, cfg.periodic, initial="plane_p_wave", precision="mixed")
+    dt = c.solver.dt_cfl()
+    u = torch_cuda(c.u0)
+    res = torch.zeros_like(u)
+    c.solver.step(u, res, dt, 10)
+    uo, ro = c.u0.copy(), np.zeros_like(c.u0)
+    for _ in range(10):
+        uo, ro = c.op.step(uo, ro, dt)
+    assert rel_l2(u.cpu().numpy(), uo) < 1e-6
+
+
+# ------------------------------------------------------------------ full size
+def test_full_size_large_workload_sampled():
+    """64^3, N=4 (the benchmark workload, same launch path): the right-hand side of a
+    random state and the first stage from the initial pulse, on sampled elements
+    (interior, free-surface and absorbing layers) computed one by one by the oracle."""
+    import torch
+    cfg = wl.large_config()
+    c = Case(cfg.E, cfg.N, cfg.amplitude, cfg.periodic, cfg.boundary, cfg.order, material=1,
+             initial="gaussian_pulse")
+    nel = c.mesh.nel
+    rng = np.random.default_rng(0)
+    bottom = np.nonzero(c.mesh.bc[:, 4] == wl.BC_ABSORBING)[0]
+    top = np.nonzero(c.mesh.bc[:, 5] == wl.BC_FREE_SURFACE)[0]
+    centre = np.nonzero(np.all(c.mesh.cell == 32, axis=1))[0]
+    sample = np.unique(np.concatenate([rng.choice(nel, 24, replace=False), rng.choice(bottom, 4),
+                                       rng.choice(top, 4), centre, [0, nel - 1]]))
+    u = wl.random_state(nel, 125, 21)
+    got = c.gpu_rhs(u)[:, sample]
+    want = c.op.rhs(u, sample)
+    assert rel_l2(got, want) < FP64_TOL
+    # first LSRK stage from the Gaussian pulse
+    ud = torch_cuda(c.u0)
+    uo_d = torch.empty_like(ud)
+    res = torch.zeros_like(ud)
+    dt = c.solver.dt_cfl()
+    c.solver.stage(ud, uo_d, res, 0, dt)
+    u1, r1 = c.op.lsrk_stage(c.u0, np.zeros_like(c.u0), 0, dt, sample)
+    assert rel_l2(uo_d.cpu().numpy()[:, sample], u1) < FP64_TOL
+    assert rel_l2(res.cpu().numpy()[:, sample], r1) < FP64_TOL
+
+
+# -------------------------------------------------------------- argument errors
+def test_call_order_and_argument_errors():
+    import torch
+    from paper_1711_01175_gb300 import DGWError, Solver
+    s = Solver(3)
+    u = torch.zeros(9, 8, 64, dtype=torch.float64, device="cuda")
+    with pytest.raises(DGWError, match="DGW_ERR_STATE"):
+        s.rhs(u, torch.empty_like(u))
+    mesh = wl.structured_hex_mesh(2)
+    from paper_1711_01175_gb300 import reference_nodes
+    r, _ = reference_nodes(3)
+    x = wl.warped_node_coords(mesh, r, 0.05)
+    bad = mesh.etoe.copy()
+    bad[0, 1] = 5
+    with pytest.raises(DGWError, match="symmetric|neighbour"):
+        s.upload_mesh(x, bad, mesh.etof, mesh.orient, mesh.bc)
+    badbc = mesh.bc.copy()
+    badbc[0, 0] = 1
+    with pytest.raises(DGWError, match="bc tag"):
+        s.upload_mesh(x, mesh.etoe, mesh.etof, mesh.orient, badbc)
+    # mirrored element: J < 0
+    xf = x.copy()
+    xf[3, :, 0] = 2 * xf[3, :, 0].mean() - xf[3, :, 0]
+    with pytest.raises(DGWError, match="Jacobian"):
+        s.upload_mesh(xf, mesh.etoe, mesh.etof, mesh.orient, mesh.bc)
+    s.upload_mesh(x, mesh.etoe, mesh.etof, mesh.orient, mesh.bc)
+    with pytest.raises(DGWError, match="DGW_ERR_STATE"):
+        s.rhs(u, torch.empty_like(u))
+    rho, lam, mu = wl.homogeneous_material(8)
+    with pytest.raises(DGWError, match="rho > 0"):
+        s.upload_material(-rho, lam, mu)
+    with pytest.raises(DGWError, match="rho > 0"):
+        s.upload_material(rho, -mu, mu)
+    s.upload_material(rho, lam, mu)
+    with pytest.raises(DGWError, match="distinct"):
+        s.rhs(u, u)
+    with pytest.raises(DGWError, match="distinct"):
+        s.stage(u, u, torch.zeros_like(u), 0, 1e-3)
+    with pytest.raises(DGWError, match="stage"):
+        s.stage(u, torch.empty_like(u), torch.zeros_like(u), 5, 1e-3)
+    from paper_1711_01175_gb300 import capi
+    assert capi.dgw_adjoint_step(s._ctx, None, None, None, None, 0.0, 0.1, 1, None) == -7
+    s.close()

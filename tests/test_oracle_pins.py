@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 import oracle
-from oracle.dg_elastic import ElasticDG, A_of, abs_A, weighted_trace, hdg_flux
+from oracle.dg_elastic import ElasticDG, A_of, abs_A, abs_A_Q, weighted_trace, hdg_flux
 import workloads as wl
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -91,6 +91,43 @@ def test_absA_invariants():
         ev = np.sort(np.linalg.eigvalsh(A))
         np.testing.assert_allclose(ev, -ev[::-1], atol=1e-13)
         assert np.sum(np.abs(ev) < 1e-12) == 3
+
+
+def test_impedance_stabilisation_axis_normal_by_hand():
+    """rho=1, lam=2, mu=1 (Zp = 2, Zs = 1), n = e1: the velocity block is
+    diag(Zp, Zs, Zs); the stress block B diag(1/Zp, 1/Zs, 1/Zs) B^T acts on
+    (s11, s13, s12) only."""
+    expect = np.diag([2, 1, 1, 0.5, 0, 0, 0, 1, 1]).astype(float)
+    np.testing.assert_allclose(abs_A_Q(np.array([1.0, 0, 0]), 1.0, 2.0, 1.0), expect, atol=1e-14)
+
+
+def test_impedance_stabilisation_is_physical_upwinding():
+    rng = np.random.default_rng(5)
+    for _ in range(10):
+        n = rng.standard_normal(3)
+        n /= np.linalg.norm(n)
+        rho, cp = rng.uniform(1, 3), rng.uniform(2, 6)
+        cs = cp / np.sqrt(3) * rng.uniform(0.9, 1.1)
+        mu, lam = rho * cs * cs, rho * (cp * cp - 2 * cs * cs)
+        A, S = A_of(n), abs_A_Q(n, rho, lam, mu)
+        Q = oracle.Q_of(rho, lam, mu)
+        Qi = np.linalg.inv(Q)
+        np.testing.assert_allclose(S, S.T, atol=1e-12)
+        assert np.min(np.linalg.eigvalsh(S)) > -1e-12
+        np.testing.assert_allclose(S @ Qi @ S, A @ Qi @ A, atol=1e-10 * np.max(np.abs(A @ Qi @ A)))
+        # |Q^{-1} A| has the physical speeds: cp twice, cs four times, three zeros
+        sp = np.sort(np.linalg.eigvals(Qi @ S).real)
+        np.testing.assert_allclose(sp, [0, 0, 0, cs, cs, cs, cs, cp, cp], atol=1e-10 * cp)
+        # characteristic upwinding: outgoing waves (speed > 0 along n) need no
+        # correction, incoming ones are replaced entirely by the exterior state
+        lamv, R = np.linalg.eig(Qi @ A)
+        for k in range(9):
+            r = R[:, k].real
+            corr = 0.5 * (A - S) @ r
+            if lamv[k].real > 1e-8:
+                assert np.max(np.abs(corr)) < 1e-10 * np.max(np.abs(A @ r) + 1)
+            elif lamv[k].real < -1e-8:
+                np.testing.assert_allclose(corr, A @ r, atol=1e-10 * np.max(np.abs(A @ r)))
 
 
 def test_hdg_flux_conservation_and_scalar_upwind():
@@ -414,7 +451,7 @@ def test_free_surface_numerical_traction_vanishes():
     um, up = op.exterior_state(u, elems, 5)
     um, up = np.moveaxis(um, 0, -1), np.moveaxis(up, 0, -1)
     An = np.einsum("...k,kij->...ij", nrm, oracle.dg_elastic.A_STACK)
-    S = abs_A(nrm)
+    S = op._abs_A_cached(elems, 5, nrm)
     F = hdg_flux(An, S, um, weighted_trace(An, S, um, up))
     assert np.max(np.abs(F[..., :3])) < 1e-13
     assert np.max(np.abs(F[..., 3:])) > 1e-3
