@@ -292,7 +292,12 @@ class ElasticDG:
         key = elems.tobytes()
         if key in self._geo_cache:
             return self._geo_cache[key]
-        X = np.moveaxis(self.x[elems], 2, 0)                  # [3, ne, Np]
+        # Element-centred coordinates: the discrete metrics are unchanged in exact
+        # arithmetic (D annihilates constants and the discrete curl of c grad X_m
+        # vanishes because D_j and D_k commute), but rounding no longer scales
+        # with |x| / h.
+        xe = self.x[elems]
+        X = np.moveaxis(xe - xe.mean(axis=1, keepdims=True), 2, 0)   # [3, ne, Np]
         dX = np.stack([self.dref(X, ax) for ax in range(3)])  # dX[axis][coord]
         Ja = np.zeros((3, 3) + X.shape[1:])
         for ncomp in range(3):
