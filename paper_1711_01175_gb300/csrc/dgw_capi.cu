@@ -52,7 +52,7 @@ void dfree(T*& p) {
 
 void free_mesh(dgw_ctx* c) {
   dfree(c->geo);
-  dfree(c->face);
+  dfree(c->fz);
   dfree(c->vmapP);
   dfree(c->wJ);
   dfree(c->u2);
@@ -83,7 +83,7 @@ dgw_status launch_stage(dgw_ctx* c, const double* u_in, double* out, double* res
   p.out = out;
   p.res = res;
   p.geo = c->geo;
-  p.face = c->face;
+  p.fz = c->fz;
   p.vmapP = c->vmapP;
   p.mat = c->mat;
   p.nel = c->nel;
@@ -327,14 +327,13 @@ dgw_status dgw_mesh_upload(dgw_ctx* c, int64_t nel, const double* x, const int64
   }
 
   const size_t nodes = (size_t)nel * Np, fnodes = (size_t)nel * 6 * nf;
-  double *x_d = nullptr, *geo64 = nullptr, *face64 = nullptr, *minJ = nullptr, *D_d = nullptr, *w_d = nullptr;
+  double *x_d = nullptr, *geo64 = nullptr, *minJ = nullptr, *D_d = nullptr, *w_d = nullptr;
   auto cleanup = [&]() {
     dfree(x_d);
     dfree(minJ);
     dfree(D_d);
     dfree(w_d);
     if (c->geo != (void*)geo64) dfree(geo64);
-    if (c->face != (void*)face64) dfree(face64);
   };
 #define DGW_TRY(call, what)                          \
   do {                                               \
@@ -347,7 +346,6 @@ dgw_status dgw_mesh_upload(dgw_ctx* c, int64_t nel, const double* x, const int64
   } while (0)
   DGW_TRY(cudaMalloc(&x_d, nodes * 3 * sizeof(double)), "alloc x");
   DGW_TRY(cudaMalloc(&geo64, nodes * 10 * sizeof(double)), "alloc geometry");
-  DGW_TRY(cudaMalloc(&face64, fnodes * 12 * sizeof(double)), "alloc face blocks");
   DGW_TRY(cudaMalloc(&c->wJ, nodes * sizeof(double)), "alloc wJ");
   DGW_TRY(cudaMalloc(&minJ, (size_t)nel * sizeof(double)), "alloc minJ");
   DGW_TRY(cudaMalloc(&D_d, sizeof(c->ref.D)), "alloc D");
@@ -359,7 +357,7 @@ dgw_status dgw_mesh_upload(dgw_ctx* c, int64_t nel, const double* x, const int64
   DGW_TRY(cudaMemcpy(D_d, c->ref.D, sizeof(c->ref.D), cudaMemcpyHostToDevice), "copy D");
   DGW_TRY(cudaMemcpy(w_d, c->ref.w, sizeof(c->ref.w), cudaMemcpyHostToDevice), "copy w");
   DGW_TRY(cudaMemcpy(c->vmapP, vmap.data(), fnodes * sizeof(int), cudaMemcpyHostToDevice), "copy neighbour map");
-  dgw::GeometryOut go{geo64, face64, c->wJ, minJ};
+  dgw::GeometryOut go{geo64, c->wJ, minJ};
   DGW_TRY(dgw::launch_geometry(N, x_d, nel, D_d, w_d, go, 0), "geometry kernel");
   DGW_TRY(cudaDeviceSynchronize(), "geometry kernel");
   std::vector<double> mj(nel);
@@ -372,21 +370,19 @@ dgw_status dgw_mesh_upload(dgw_ctx* c, int64_t nel, const double* x, const int64
     }
   }
   if (c->cfg.precision == DGW_PRECISION_MIXED) {
-    float *g32 = nullptr, *f32 = nullptr;
+    float* g32 = nullptr;
     DGW_TRY(cudaMalloc(&g32, nodes * 10 * sizeof(float)), "alloc geometry fp32");
     c->geo = g32;
-    DGW_TRY(cudaMalloc(&f32, fnodes * 12 * sizeof(float)), "alloc face fp32");
-    c->face = f32;
     DGW_TRY(dgw::launch_to_float(geo64, g32, nodes * 10, 0), "geometry to fp32");
-    DGW_TRY(dgw::launch_to_float(face64, f32, fnodes * 12, 0), "face to fp32");
     DGW_TRY(cudaDeviceSynchronize(), "geometry to fp32");
   } else {
     c->geo = geo64;
-    c->face = face64;
   }
   cleanup();
 #undef DGW_TRY
   c->nel = nel;
+  c->etoe.assign(etoe, etoe + nel * 6);
+  c->bc.assign(bc, bc + nel * 6);
   c->h_min = hmin;
   c->has_mesh = true;
   c->has_material = false;
@@ -412,19 +408,42 @@ dgw_status dgw_material_upload(dgw_ctx* c, const double* rho, const double* lam,
     ec[3 * nel + e] = 1.0 / mu[e];
     cmax = std::fmax(cmax, std::sqrt((lam[e] + 2.0 * mu[e]) / rho[e]));
   }
+  // Face media: the average of the two sides' (rho, lam, mu) on interior faces,
+  // the element's own on boundary faces; impedances Zp = sqrt(rho (lam + 2 mu)),
+  // Zs = sqrt(rho mu) of that medium.
+  std::vector<double> fz(4 * 6 * nel);
+  const size_t fzs = 6 * (size_t)nel;
+  for (long long e = 0; e < nel; ++e) {
+    for (int f = 0; f < 6; ++f) {
+      const long long k = e * 6 + f;
+      const long long o = (c->etoe[k] >= 0 && c->bc[k] == DGW_BC_INTERIOR) ? c->etoe[k] : e;
+      const double r = 0.5 * (rho[e] + rho[o]), l = 0.5 * (lam[e] + lam[o]), m = 0.5 * (mu[e] + mu[o]);
+      const double zp = std::sqrt(r * (l + 2.0 * m)), zs = std::sqrt(r * m);
+      fz[k] = zs;
+      fz[fzs + k] = zp - zs;
+      fz[2 * fzs + k] = 1.0 / zs;
+      fz[3 * fzs + k] = 1.0 / zp - 1.0 / zs;
+    }
+  }
   if (set_device(c) != DGW_OK) return DGW_ERR_CUDA;
   dfree(c->mat);
   dfree(c->ec);
+  dfree(c->fz);
   c->has_material = false;
   DGW_CUDA(c, cudaMalloc(&c->ec, 4 * nel * sizeof(double)), "alloc energy constants");
   DGW_CUDA(c, cudaMemcpy(c->ec, ec.data(), 4 * nel * sizeof(double), cudaMemcpyHostToDevice), "copy energy constants");
   if (c->cfg.precision == DGW_PRECISION_MIXED) {
     std::vector<float> m32(m64.begin(), m64.end());
+    std::vector<float> fz32(fz.begin(), fz.end());
     DGW_CUDA(c, cudaMalloc(&c->mat, 3 * nel * sizeof(float)), "alloc material");
     DGW_CUDA(c, cudaMemcpy(c->mat, m32.data(), 3 * nel * sizeof(float), cudaMemcpyHostToDevice), "copy material");
+    DGW_CUDA(c, cudaMalloc(&c->fz, fz32.size() * sizeof(float)), "alloc face media");
+    DGW_CUDA(c, cudaMemcpy(c->fz, fz32.data(), fz32.size() * sizeof(float), cudaMemcpyHostToDevice), "copy face media");
   } else {
     DGW_CUDA(c, cudaMalloc(&c->mat, 3 * nel * sizeof(double)), "alloc material");
     DGW_CUDA(c, cudaMemcpy(c->mat, m64.data(), 3 * nel * sizeof(double), cudaMemcpyHostToDevice), "copy material");
+    DGW_CUDA(c, cudaMalloc(&c->fz, fz.size() * sizeof(double)), "alloc face media");
+    DGW_CUDA(c, cudaMemcpy(c->fz, fz.data(), fz.size() * sizeof(double), cudaMemcpyHostToDevice), "copy face media");
   }
   c->c_max = cmax;
   c->has_material = true;

@@ -6,54 +6,14 @@
 //     conservative curl form  J a^i_n = -[curl_xi (X_l grad_xi X_m)]_i,
 //     (n, m, l) cyclic -- with the same D, so sum_i D_i (J a^i_k) = 0 holds
 //     to round-off (free-stream preservation on curved elements);
-//   * J = det(dX/dxi), 1/J and the mass weights w_i w_j w_k J;
-//   * on every face node the scaled outward normal m = n sJ = +-J a^d and the
-//     stabilisation blocks P = (B(m)^T B(m))^{1/2} and P^{-1}, where B(m) is
-//     the 6x3 strain map of the normal: |A(m)| = diag(P, B P^{-1} B^T).
-#include <cmath>
-
+//   * J = det(dX/dxi), 1/J and the mass weights w_i w_j w_k J.
+// The scaled outward normal of a face node, m = n sJ = +-J a^d, is read from
+// the same metric array by the stage kernel.
 #include "dgw_internal.cuh"
 
 namespace dgw {
 
 namespace {
-
-// Symmetric 3x3 eigen-decomposition by cyclic Jacobi rotations (FP64).
-__device__ void sym3_eig(double a[3][3], double V[3][3], double lam[3]) {
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) V[i][j] = (i == j) ? 1.0 : 0.0;
-  for (int sweep = 0; sweep < 32; ++sweep) {
-    const double off = a[0][1] * a[0][1] + a[0][2] * a[0][2] + a[1][2] * a[1][2];
-    const double dia = a[0][0] * a[0][0] + a[1][1] * a[1][1] + a[2][2] * a[2][2];
-    if (off <= 1e-34 * dia) break;
-    for (int p = 0; p < 2; ++p) {
-      for (int q = p + 1; q < 3; ++q) {
-        const double apq = a[p][q];
-        if (apq == 0.0) continue;
-        const double theta = (a[q][q] - a[p][p]) / (2.0 * apq);
-        const double tt = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-        const double c = 1.0 / sqrt(tt * tt + 1.0);
-        const double s = tt * c;
-        for (int k = 0; k < 3; ++k) {           // A <- A J  (columns p, q)
-          const double akp = a[k][p], akq = a[k][q];
-          a[k][p] = c * akp - s * akq;
-          a[k][q] = s * akp + c * akq;
-        }
-        for (int k = 0; k < 3; ++k) {           // A <- J^T A (rows p, q)
-          const double apk = a[p][k], aqk = a[q][k];
-          a[p][k] = c * apk - s * aqk;
-          a[q][k] = s * apk + c * aqk;
-        }
-        for (int k = 0; k < 3; ++k) {           // V <- V J
-          const double vkp = V[k][p], vkq = V[k][q];
-          V[k][p] = c * vkp - s * vkq;
-          V[k][q] = s * vkp + c * vkq;
-        }
-      }
-    }
-  }
-  for (int i = 0; i < 3; ++i) lam[i] = a[i][i];
-}
 
 template <int N>
 __global__ void geometry_kernel(const double* __restrict__ x, long long nel, GeometryOut out,
@@ -71,6 +31,17 @@ __global__ void geometry_kernel(const double* __restrict__ x, long long nel, Geo
   for (int i = t; i < n * n; i += blockDim.x) D[i] = Dg[i];
   for (int i = t; i < n; i += blockDim.x) w[i] = wg[i];
   for (int i = t; i < 3 * Np; i += blockDim.x) Xs[i % 3][i / 3] = x[(size_t)e * Np * 3 + i];
+  __syncthreads();
+  // Coordinates relative to the element's first node: the discrete metrics are
+  // translation invariant in exact arithmetic (D annihilates constants; the
+  // discrete curl of c grad X_m vanishes), and rounding stops scaling with |x|/h.
+  const double x0 = Xs[0][0], y0 = Xs[1][0], z0 = Xs[2][0];
+  __syncthreads();
+  for (int i = t; i < Np; i += blockDim.x) {
+    Xs[0][i] -= x0;
+    Xs[1][i] -= y0;
+    Xs[2][i] -= z0;
+  }
   __syncthreads();
 
   const int ix = t % n, iy = (t / n) % n, iz = t / nf;
@@ -122,40 +93,6 @@ __global__ void geometry_kernel(const double* __restrict__ x, long long nel, Geo
     out.minJ[e] = mn;
   }
 
-  // Face stabilisation blocks.
-  const size_t ffstride = (size_t)nel * 6 * nf;
-  for (int it = t; it < 6 * nf; it += blockDim.x) {
-    const int f = it / nf, pf = it % nf;
-    const int d = f >> 1;
-    const bool hi = f & 1;
-    const int fa = pf % n, fb = pf / n, cd = hi ? N : 0;
-    const int c0 = d == 0 ? cd : fa;
-    const int c1 = d == 0 ? fa : (d == 1 ? cd : fb);
-    const int c2 = d == 2 ? cd : fb;
-    const int vn = c0 + n * (c1 + n * c2);
-    const double sgn = hi ? 1.0 : -1.0;
-    const double m0 = sgn * Jas[3 * d + 0][vn], m1 = sgn * Jas[3 * d + 1][vn],
-                 m2 = sgn * Jas[3 * d + 2][vn];
-    const double mm = m0 * m0 + m1 * m1 + m2 * m2;
-    // B^T B = |m|^2 I + m m^T - diag(m^2)
-    double C[3][3] = {{mm, m0 * m1, m0 * m2}, {m0 * m1, mm, m1 * m2}, {m0 * m2, m1 * m2, mm}};
-    double V[3][3], lam[3];
-    sym3_eig(C, V, lam);
-    double sq[3], isq[3];
-    for (int k = 0; k < 3; ++k) {
-      sq[k] = sqrt(fmax(lam[k], 0.0));
-      isq[k] = sq[k] > 0.0 ? 1.0 / sq[k] : 0.0;
-    }
-    auto entry = [&](const double* s, int i, int j) {
-      return V[i][0] * s[0] * V[j][0] + V[i][1] * s[1] * V[j][1] + V[i][2] * s[2] * V[j][2];
-    };
-    const int pairs[6][2] = {{0, 0}, {1, 1}, {2, 2}, {1, 2}, {0, 2}, {0, 1}};
-    const size_t fi = (size_t)e * 6 * nf + it;
-    for (int c = 0; c < 6; ++c) {
-      out.face[c * ffstride + fi] = entry(sq, pairs[c][0], pairs[c][1]);
-      out.face[(6 + c) * ffstride + fi] = entry(isq, pairs[c][0], pairs[c][1]);
-    }
-  }
 }
 
 __global__ void to_float_kernel(const double* __restrict__ src, float* __restrict__ dst, size_t n) {

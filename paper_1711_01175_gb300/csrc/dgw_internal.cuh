@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include "dgw.h"
 
@@ -46,7 +47,7 @@ struct StageParams {
   double* out;            // rhs (rhs mode) or u_out (LSRK mode), [9][nel][Np]
   double* res;            // LSRK register [9][nel][Np] (LSRK mode only)
   const void* geo;        // Real [10][nel][Np]: Ja^i_k at 3*i+k, then 1/J
-  const void* face;       // Real [12][nel][6*nf]: P (xx,yy,zz,yz,xz,xy), then P^{-1}
+  const void* fz;         // Real [4][nel*6]: Zs, Zp-Zs, 1/Zs, 1/Zp-1/Zs of the face medium
   const int* vmapP;       // [nel][6*nf]: neighbour flat node index or ghost sentinel
   const void* mat;        // Real [3][nel]: 1/rho, lambda, mu
   long long nel;
@@ -64,7 +65,6 @@ void stage_shape(int N, int* epb, int* threads);
 // Geometry (dgw_geometry.cu).
 struct GeometryOut {
   double* geo;       // [10][nel][Np]  Ja (9) then 1/J
-  double* face;      // [12][nel][6*nf] P then P^{-1}
   double* wJ;        // [nel][Np]       w_i w_j w_k J
   double* minJ;      // [nel]
 };
@@ -89,7 +89,7 @@ struct dgw_ctx {
   bool has_material = false;
   // device memory owned by the context
   void* geo = nullptr;       // Real [10][nel][Np]
-  void* face = nullptr;      // Real [12][nel][6*nf]
+  void* fz = nullptr;        // Real [4][nel*6] face impedance constants
   int* vmapP = nullptr;      // [nel][6*nf]
   void* mat = nullptr;       // Real [3][nel]
   double* ec = nullptr;      // [4][nel] energy constants: rho, 1/(2 mu), lam/(3 lam + 2 mu), 1/mu
@@ -99,6 +99,8 @@ struct dgw_ctx {
   double* stage_u = nullptr;   // host-pointer staging buffers
   double* stage_res = nullptr;
   double* pinned = nullptr;    // pinned host slot for the energy value
+  std::vector<int64_t> etoe;   // host copy of the connectivity (face media)
+  std::vector<int8_t> bc;
   double h_min = 0.0;
   double c_max = 0.0;
   std::string err;

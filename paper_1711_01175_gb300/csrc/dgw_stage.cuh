@@ -9,9 +9,10 @@
 //      and vol = -1/2 * (1/J) * acc.  A(m)u = -(sigma m, Voigt(sym(m (x) v))).
 //   3. Face items (EPB*6*nf of them, spread over all threads): own trace from
 //      smem, neighbour trace from HBM/L2 through the neighbour map (or the
-//      boundary ghost), flux difference 1/2 (A(m) - tau |A(m)|)(u^- - u^+) with
-//      m = n sJ the scaled outward normal and |A(m)| = diag(P, B P^{-1} B^T),
-//      P = (B^T B)^{1/2} -- the upwind HDG flux of eq. RiemannFluxBoth with the
+//      boundary ghost), flux difference 1/2 (A(m) - tau S(m))(u^- - u^+) with
+//      m = n sJ the scaled outward normal and S(m) = sJ Q|Q^{-1}A(n)| the
+//      impedance-weighted upwind stabilisation of the face medium -- the upwind
+//      HDG flux of eq. RiemannFluxBoth (for the flux matrix Q^{-1}A(n)) with the
 //      trace eliminated by eq. HDGeqn/iHDGtrace -- scaled by the lift factor
 //      (1/J)/w_0 and staged in smem.
 //   4. Each node adds the lifted flux of the faces it lies on, applies
@@ -144,8 +145,7 @@ __global__ void __launch_bounds__(Shape<N>::NT) stage_kernel(const StageParams p
 
   // Face items: lifted flux differences.
   {
-    const Real* face = static_cast<const Real*>(p.face);
-    const size_t ffstride = static_cast<size_t>(p.nel) * 6 * nf;
+    const Real* fz = static_cast<const Real*>(p.fz);
     const Real tau = static_cast<Real>(p.tau);
     const Real half_lift = static_cast<Real>(0.5 * p.w_end_inv);
     for (int it = t; it < NFI; it += NT) {
@@ -190,29 +190,32 @@ __global__ void __launch_bounds__(Shape<N>::NT) stage_kernel(const StageParams p
       Real Ad[9];
       apply_Apos(m1, m2, m3, du, Ad);      // A_+(m) du = -A(m) du
       Real flux[9];
+      const Real s = -half_lift * jv;
       if (tau != Real(0)) {
-        const size_t fi = static_cast<size_t>(ei) * 6 * nf + r;
-        Real P[6], Pi[6];
+        // Impedance-weighted upwind stabilisation S(m) = sJ Q|Q^{-1}A(n)| of the
+        // face medium (Zp = rho cp, Zs = rho cs):
+        //   velocity rows  sJ [Zs dv + (Zp - Zs)(n.dv) n]
+        //   stress rows    sJ B(n) [y/Zs + (1/Zp - 1/Zs)(n.y) n],  y = B(n)^T dsigma.
+        const size_t fzi = static_cast<size_t>(ei) * 6 + f;
+        const size_t fzs = static_cast<size_t>(p.nel) * 6;
+        const Real zs = fz[fzi], dz = fz[fzs + fzi], izs = fz[2 * fzs + fzi], diz = fz[3 * fzs + fzi];
+        const Real mm = m1 * m1 + m2 * m2 + m3 * m3;
+        const Real isJ = Real(1) / sqrt(mm);
+        const Real sJ = mm * isJ;
+        const Real av = dz * (m1 * du[0] + m2 * du[1] + m3 * du[2]) * isJ;
+        const Real zsJ = zs * sJ;
+        // y = dsigma m = Ad[0..2] (scaled by sJ); z = isJ (y/Zs + (1/Zp-1/Zs)(m.y) m / sJ^2)
+        const Real by = diz * (m1 * Ad[0] + m2 * Ad[1] + m3 * Ad[2]) * isJ * isJ;
+        const Real z0 = isJ * (izs * Ad[0] + by * m1);
+        const Real z1 = isJ * (izs * Ad[1] + by * m2);
+        const Real z2 = isJ * (izs * Ad[2] + by * m3);
+        const Real Sd[9] = {zsJ * du[0] + av * m1, zsJ * du[1] + av * m2, zsJ * du[2] + av * m3,
+                            m1 * z0, m2 * z1, m3 * z2,
+                            m2 * z2 + m3 * z1, m1 * z2 + m3 * z0, m1 * z1 + m2 * z0};
+        // 1/2 (A(m) - tau S(m)) du (1/J)/w_0 = -1/2 (A_+ du + tau S du) (1/J)/w_0
 #pragma unroll
-        for (int c = 0; c < 6; ++c) {
-          P[c] = face[c * ffstride + fi];
-          Pi[c] = face[(6 + c) * ffstride + fi];
-        }
-        // |A(m)| du = (P dv, B P^{-1} B^T dsigma); B^T dsigma = dsigma m = Ad[0..2]
-        const Real pv0 = P[0] * du[0] + P[5] * du[1] + P[4] * du[2];
-        const Real pv1 = P[5] * du[0] + P[1] * du[1] + P[3] * du[2];
-        const Real pv2 = P[4] * du[0] + P[3] * du[1] + P[2] * du[2];
-        const Real z0 = Pi[0] * Ad[0] + Pi[5] * Ad[1] + Pi[4] * Ad[2];
-        const Real z1 = Pi[5] * Ad[0] + Pi[1] * Ad[1] + Pi[3] * Ad[2];
-        const Real z2 = Pi[4] * Ad[0] + Pi[3] * Ad[1] + Pi[2] * Ad[2];
-        const Real absd[9] = {pv0, pv1, pv2, m1 * z0, m2 * z1, m3 * z2,
-                              m2 * z2 + m3 * z1, m1 * z2 + m3 * z0, m1 * z1 + m2 * z0};
-        // 1/2 (A(m) - tau|A(m)|) du * (1/J)/w_0 = -1/2 (A_+ du + tau |A| du) (1/J)/w_0
-        const Real s = -half_lift * jv;
-#pragma unroll
-        for (int q = 0; q < 9; ++q) flux[q] = s * (Ad[q] + tau * absd[q]);
+        for (int q = 0; q < 9; ++q) flux[q] = s * (Ad[q] + tau * Sd[q]);
       } else {
-        const Real s = -half_lift * jv;
 #pragma unroll
         for (int q = 0; q < 9; ++q) flux[q] = s * Ad[q];
       }
