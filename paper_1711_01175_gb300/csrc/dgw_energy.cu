@@ -25,19 +25,20 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return s;   // valid in thread 0
 }
 
+template <int Np>
 __global__ void __launch_bounds__(kEnergyThreads)
 energy_partial_kernel(const double* __restrict__ u, const double* __restrict__ wJ,
-                      const double* __restrict__ ec, long long nel, int Np, double* partials) {
+                      const double* __restrict__ ec, long long nel, double* partials) {
   __shared__ double red[32];
-  const size_t total = (size_t)nel * Np;
+  const unsigned total = (unsigned)(nel * Np);   // nel * Np < 2^31 (checked at upload)
   double acc = 0.0;
-  for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total;
-       g += (size_t)gridDim.x * blockDim.x) {
-    const long long e = (long long)(g / Np);
+  for (unsigned g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
+    const unsigned e = g / Np;
     const double rho = ec[e], i2mu = ec[nel + e], lfac = ec[2 * nel + e], imu = ec[3 * nel + e];
-    const double v1 = u[g], v2 = u[total + g], v3 = u[2 * total + g];
-    const double s1 = u[3 * total + g], s2 = u[4 * total + g], s3 = u[5 * total + g];
-    const double s4 = u[6 * total + g], s5 = u[7 * total + g], s6 = u[8 * total + g];
+    const size_t T = total;   // field stride; 9 * T may exceed 2^32
+    const double v1 = u[g], v2 = u[T + g], v3 = u[2 * T + g];
+    const double s1 = u[3 * T + g], s2 = u[4 * T + g], s3 = u[5 * T + g];
+    const double s4 = u[6 * T + g], s5 = u[7 * T + g], s6 = u[8 * T + g];
     const double tr = s1 + s2 + s3;
     const double kin = rho * (v1 * v1 + v2 * v2 + v3 * v3);
     const double pot = i2mu * (s1 * s1 + s2 * s2 + s3 * s3 - lfac * tr * tr) +
@@ -61,7 +62,16 @@ energy_final_kernel(const double* __restrict__ partials, int nparts, double* res
 
 cudaError_t launch_energy(const double* u, const double* wJ, const double* ec, long long nel, int Np,
                           double* partials, double* result, cudaStream_t s) {
-  energy_partial_kernel<<<kEnergyBlocks, kEnergyThreads, 0, s>>>(u, wJ, ec, nel, Np, partials);
+  switch (Np) {
+#define DGW_EN(NP)                                                                         \
+  case NP:                                                                                 \
+    energy_partial_kernel<NP><<<kEnergyBlocks, kEnergyThreads, 0, s>>>(u, wJ, ec, nel, partials); \
+    break;
+    DGW_EN(8) DGW_EN(27) DGW_EN(64) DGW_EN(125) DGW_EN(216) DGW_EN(343) DGW_EN(512)
+#undef DGW_EN
+    default:
+      return cudaErrorInvalidValue;
+  }
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   energy_final_kernel<<<1, kEnergyThreads, 0, s>>>(partials, kEnergyBlocks, result);

@@ -40,6 +40,37 @@ __device__ __forceinline__ void apply_Apos(Real m1, Real m2, Real m3, const Real
   out[8] = m1 * w[1] + m2 * w[0];
 }
 
+// FP64 -> FP32 (round to nearest on the dropped 29 bits, flush below the
+// smallest normal float) and FP32 -> FP64 (exact) with integer instructions.
+// The GB300 FP64 pipe, which also executes the F2F conversions, issues about
+// two operations per clock per SM; integer operations are much wider.
+__device__ __forceinline__ float narrow_int(double d) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(d));
+  const unsigned sign = static_cast<unsigned>(b >> 32) & 0x80000000u;
+  const unsigned long long mag = b & 0x7fffffffffffffffull;
+  long long f = static_cast<long long>((mag + (1ull << 28)) >> 29) - (896ll << 23);
+  f = f < (1ll << 23) ? 0ll : (f > 0x7f800000ll ? 0x7f800000ll : f);
+  return __uint_as_float(static_cast<unsigned>(f) | sign);
+}
+
+__device__ __forceinline__ double widen_int(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned long long sign = static_cast<unsigned long long>(u & 0x80000000u) << 32;
+  unsigned long long mag = static_cast<unsigned long long>(u & 0x7fffffffu) << 29;
+  mag = (e == 255u) ? (mag | 0x7ff0000000000000ull) : (mag + (896ull << 52));
+  return __longlong_as_double(static_cast<long long>(e == 0u ? sign : (sign | mag)));
+}
+
+template <typename Real>
+__device__ __forceinline__ Real to_real(double d) {
+  if constexpr (std::is_same<Real, double>::value) {
+    return d;
+  } else {
+    return narrow_int(d);
+  }
+}
+
 template <int N, typename Real, bool LSRK>
 __global__ void __launch_bounds__(Shape<N>::NT) stage_kernel(const StageParams p) {
   using S = Shape<N>;
@@ -73,7 +104,7 @@ __global__ void __launch_bounds__(Shape<N>::NT) stage_kernel(const StageParams p
     for (int q = 0; q < 9; ++q) {
       const double v = p.u_in[q * fstride + gidx];
       if constexpr (LSRK && !std::is_same<Real, double>::value) u_keep[q] = v;
-      u_s[q * NTILE + t] = static_cast<Real>(v);
+      u_s[q * NTILE + t] = to_real<Real>(v);
     }
 #pragma unroll
     for (int c = 0; c < 9; ++c) ja[c] = geo[c * fstride + gidx];
@@ -170,7 +201,7 @@ __global__ void __launch_bounds__(Shape<N>::NT) stage_kernel(const StageParams p
       if (g >= 0) {
 #pragma unroll
         for (int q = 0; q < 9; ++q)
-          du[q] = u_s[q * NTILE + sidx] - static_cast<Real>(p.u_in[q * fstride + g]);
+          du[q] = u_s[q * NTILE + sidx] - to_real<Real>(p.u_in[q * fstride + g]);
       } else if (g == kGhostFreeSurface) {
         // exterior (v, -sigma): jump (0, 2 sigma)
 #pragma unroll
@@ -249,34 +280,45 @@ __global__ void __launch_bounds__(Shape<N>::NT) stage_kernel(const StageParams p
   const Real irho = mat[e];
   const Real lam = mat[p.nel + e];
   const Real mu = mat[2 * p.nel + e];
-  double rhs[9];
-  rhs[0] = static_cast<double>(irho * r[0]);
-  rhs[1] = static_cast<double>(irho * r[1]);
-  rhs[2] = static_cast<double>(irho * r[2]);
+  Real rr[9];
+  rr[0] = irho * r[0];
+  rr[1] = irho * r[1];
+  rr[2] = irho * r[2];
   const Real tr = r[3] + r[4] + r[5];
   const Real two_mu = mu + mu;
-  rhs[3] = static_cast<double>(lam * tr + two_mu * r[3]);
-  rhs[4] = static_cast<double>(lam * tr + two_mu * r[4]);
-  rhs[5] = static_cast<double>(lam * tr + two_mu * r[5]);
-  rhs[6] = static_cast<double>(mu * r[6]);
-  rhs[7] = static_cast<double>(mu * r[7]);
-  rhs[8] = static_cast<double>(mu * r[8]);
+  rr[3] = lam * tr + two_mu * r[3];
+  rr[4] = lam * tr + two_mu * r[4];
+  rr[5] = lam * tr + two_mu * r[5];
+  rr[6] = mu * r[6];
+  rr[7] = mu * r[7];
+  rr[8] = mu * r[8];
 
   if constexpr (!LSRK) {
 #pragma unroll
-    for (int q = 0; q < 9; ++q) p.out[q * fstride + gidx] = rhs[q];
+    for (int q = 0; q < 9; ++q) {
+      if constexpr (std::is_same<Real, double>::value) {
+        p.out[q * fstride + gidx] = rr[q];
+      } else {
+        p.out[q * fstride + gidx] = widen_int(rr[q]);
+      }
+    }
   } else {
+    // res <- a res + dt rhs; u_out <- u_in + b res, both FP64.  a_0 = 0: the
+    // incoming register is not read in the first stage.
+    const bool first = p.a == 0.0;
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
-      double uq;
+      double uq, dtr;
       if constexpr (std::is_same<Real, double>::value) {
         uq = u_s[q * NTILE + t];
+        dtr = p.dt * rr[q];
       } else {
         uq = u_keep[q];
+        dtr = widen_int(static_cast<float>(p.dt) * rr[q]);
       }
-      const double rn = p.a * p.res[q * fstride + gidx] + p.dt * rhs[q];
+      const double rn = first ? dtr : fma(p.a, p.res[q * fstride + gidx], dtr);
       p.res[q * fstride + gidx] = rn;
-      p.out[q * fstride + gidx] = uq + p.b * rn;
+      p.out[q * fstride + gidx] = fma(p.b, rn, uq);
     }
   }
 }

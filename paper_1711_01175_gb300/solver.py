@@ -90,6 +90,8 @@ class Solver:
         self._check(capi.dgw_material_upload(self._ctx, *[_ptr(a) for a in arrs]))
 
     def _field_check(self, a, name):
+        if self.nel == 0:
+            return          # no mesh yet: the C ABI reports the call-order error
         shape = tuple(a.shape)
         if shape != (9, self.nel, self.Np):
             raise ValueError(f"{name} must be [9, {self.nel}, {self.Np}], got {shape}")
