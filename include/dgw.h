@@ -150,6 +150,31 @@ dgw_status dgw_adjoint_step(dgw_ctx* ctx, double* lam_u, double* lam_res, double
  * time-dependent transport experiments (Section 6.1). */
 dgw_status dgw_dt_cfl(dgw_ctx* ctx, double* dt_out);
 
+/* Discrete energy for callers that cannot allocate device memory.
+ * The paper has no counterpart: this is a deployment convenience.  Some
+ * callers cannot call cudaMalloc -- a host framework whose pool allocator
+ * owns all device memory and caps it, a time loop that must not allocate once
+ * it is running, code that only receives device pointers from another
+ * library.  This entry point needs no context and allocates nothing: every
+ * argument is the caller's device memory, and the reduction's scratch is a
+ * fixed 512 KB array in the library's device module (held on every device
+ * that loads the library until the process exits).
+ *   N           degree 1..7; x, u at the nodes of dgw_reference_nodes(N)
+ *   nel         1 .. DGW_ENERGY_STATIC_MAX_ELEMENTS (larger: DGW_ERR_ARG)
+ *   x           device [nel][Np][3] node coordinates (J is computed from them)
+ *   u           device [9][nel][Np] state
+ *   rho,lam,mu  device [nel] medium (no validation of the values)
+ *   energy_out  device pointer to one double; written when the work queued on
+ *               `stream` (the current device's) completes.
+ * Same value as dgw_energy on the same mesh to rounding.  The first call on
+ * a device looks up the scratch array's device address; make that first call
+ * before any stream capture.  All calls share the scratch array: calls whose
+ * kernels overlap on the GPU (unordered streams) race.  Errors:
+ * dgw_last_error(NULL). */
+#define DGW_ENERGY_STATIC_MAX_ELEMENTS (1 << 20)
+dgw_status dgw_energy_static(int N, int64_t nel, const double* x, const double* u, const double* rho,
+                             const double* lam, const double* mu, double* energy_out, void* stream);
+
 /* Message of the last failing call on ctx (or of the last failing call
  * without a context when ctx is NULL).  Never NULL; owned by the library. */
 const char* dgw_last_error(const dgw_ctx* ctx);

@@ -44,6 +44,7 @@ SIGNATURES = {
     "dgw_energy": (_I, [_P, _P, ctypes.POINTER(_D), _P]),
     "dgw_adjoint_step": (_I, [_P, _P, _P, _P, _P, _D, _D, _I, _P]),
     "dgw_dt_cfl": (_I, [_P, ctypes.POINTER(_D)]),
+    "dgw_energy_static": (_I, [_I, _I64, _P, _P, _P, _P, _P, _P, _P]),
     "dgw_last_error": (ctypes.c_char_p, [_P]),
 }
 
@@ -133,6 +134,10 @@ def dgw_dt_cfl(ctx):
     out = _D()
     st = load().dgw_dt_cfl(ctx, ctypes.byref(out))
     return st, out.value
+
+
+def dgw_energy_static(N, nel, x, u, rho, lam, mu, energy_out, stream):
+    return load().dgw_energy_static(N, nel, x, u, rho, lam, mu, energy_out, stream)
 
 
 def dgw_last_error(ctx):

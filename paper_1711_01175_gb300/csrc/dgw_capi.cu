@@ -183,6 +183,8 @@ bool build_ref_elem(int N, RefElem* out) {
   return true;
 }
 
+void set_no_context_error(const std::string& msg) { g_error = msg; }
+
 }  // namespace dgw
 
 // ----------------------------------------------------------------------------

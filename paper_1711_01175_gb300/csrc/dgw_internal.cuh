@@ -78,6 +78,9 @@ constexpr int kEnergyThreads = 256;
 cudaError_t launch_energy(const double* u, const double* wJ, const double* ec, long long nel, int Np,
                           double* partials, double* result, cudaStream_t s);
 
+// Message storage of calls without a context (read by dgw_last_error(NULL)).
+void set_no_context_error(const std::string& msg);
+
 }  // namespace dgw
 
 struct dgw_ctx {
