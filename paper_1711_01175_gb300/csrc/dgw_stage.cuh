@@ -71,17 +71,82 @@ __device__ __forceinline__ Real to_real(double d) {
   }
 }
 
+// Node-major packed tiles: PK Reals per node, read and written as 16-byte
+// vectors (3 x float4 for FP32, 5 x double2 for FP64).  Strides of 48 B and
+// 80 B keep eight consecutive nodes on distinct 16-byte bank groups.
+template <typename Real>
+struct Pack;
+template <>
+struct Pack<float> {
+  static constexpr int PK = 12;
+  static __device__ __forceinline__ void load9(const float* p, float* v) {
+    const float4 a = reinterpret_cast<const float4*>(p)[0];
+    const float4 b = reinterpret_cast<const float4*>(p)[1];
+    const float4 c = reinterpret_cast<const float4*>(p)[2];
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    v[8] = c.x; v[9] = c.y;
+  }
+  static __device__ __forceinline__ void store10(float* p, const float* v) {
+    reinterpret_cast<float4*>(p)[0] = make_float4(v[0], v[1], v[2], v[3]);
+    reinterpret_cast<float4*>(p)[1] = make_float4(v[4], v[5], v[6], v[7]);
+    reinterpret_cast<float4*>(p)[2] = make_float4(v[8], v[9], 0.f, 0.f);
+  }
+};
+template <>
+struct Pack<double> {
+  static constexpr int PK = 10;
+  static __device__ __forceinline__ void load9(const double* p, double* v) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const double2 a = reinterpret_cast<const double2*>(p)[k];
+      v[2 * k] = a.x;
+      v[2 * k + 1] = a.y;
+    }
+  }
+  static __device__ __forceinline__ void store10(double* p, const double* v) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) reinterpret_cast<double2*>(p)[k] = make_double2(v[2 * k], v[2 * k + 1]);
+  }
+};
+
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+template <int N, typename Real>
+struct StageSmem {
+  using S = Shape<N>;
+  static constexpr int PK = Pack<Real>::PK;
+  static constexpr bool kPrefetchRes = std::is_same<Real, float>::value;
+  static constexpr size_t u_off = 0;                                    // Real [NTILE][PK] state
+  static constexpr size_t f_off = u_off + sizeof(Real) * S::NTILE * PK;  // Real [NTILE][PK] flux / face fluxes
+  static constexpr size_t fbytes = sizeof(Real) * (S::NTILE * PK > 9 * S::NFACE_ITEMS ? S::NTILE * PK : 9 * S::NFACE_ITEMS);
+  static constexpr size_t g_off = f_off + ((fbytes + 15) / 16) * 16;     // Real [NTILE][PK] Ja, 1/J
+  static constexpr size_t d_off = g_off + sizeof(Real) * S::NTILE * PK;  // Real [n*n]
+  static constexpr size_t r_off = ((d_off + sizeof(Real) * S::n * S::n + 15) / 16) * 16;  // double [9][NTILE]
+  static constexpr size_t bytes = r_off + (kPrefetchRes ? sizeof(double) * 9 * S::NTILE : 0);
+};
+
 template <int N, typename Real, bool LSRK>
 __global__ void __launch_bounds__(Shape<N>::NT) stage_kernel(const StageParams p) {
   using S = Shape<N>;
+  using L = StageSmem<N, Real>;
+  using V = Pack<Real>;
   constexpr int n = S::n, Np = S::Np, nf = S::nf, EPB = S::EPB, NT = S::NT;
-  constexpr int NTILE = S::NTILE, NFI = S::NFACE_ITEMS;
+  constexpr int NTILE = S::NTILE, NFI = S::NFACE_ITEMS, PK = L::PK;
+  constexpr bool kPrefetch = LSRK && L::kPrefetchRes;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Real* u_s = reinterpret_cast<Real*>(smem_raw);   // [9][NTILE]
-  Real* f_s = u_s + 9 * NTILE;                      // [10][NTILE]: flux, later Ja + 1/J
-  Real* x_s = f_s + 10 * NTILE;                     // [9][NFI]: lifted face flux
-  Real* D_s = x_s + 9 * NFI;                        // [n*n]
+  Real* u_s = reinterpret_cast<Real*>(smem_raw + L::u_off);
+  Real* f_s = reinterpret_cast<Real*>(smem_raw + L::f_off);
+  Real* x_s = f_s;                       // face fluxes [9][NFI] reuse the flux tile
+  Real* g_s = reinterpret_cast<Real*>(smem_raw + L::g_off);
+  Real* D_s = reinterpret_cast<Real*>(smem_raw + L::d_off);
+  double* r_s = reinterpret_cast<double*>(smem_raw + L::r_off);
 
   const int t = threadIdx.x;
   for (int i = t; i < n * n; i += NT) D_s[i] = static_cast<Real>(p.D[i]);
@@ -95,27 +160,31 @@ __global__ void __launch_bounds__(Shape<N>::NT) stage_kernel(const StageParams p
   const size_t fstride = static_cast<size_t>(p.nel) * Np;
   const size_t gidx = active ? static_cast<size_t>(e) * Np + node : 0;
   const Real* geo = static_cast<const Real*>(p.geo);
+  const bool first = p.a == 0.0;
 
-  double u_keep[LSRK && !std::is_same<Real, double>::value ? 9 : 1];
-  Real ja[9];
-  Real jinv = 0;
-  if (active) {
+  if constexpr (kPrefetch) {
+    // The register res is needed only in the epilogue: start its copy now.
+    if (active && !first) {
 #pragma unroll
-    for (int q = 0; q < 9; ++q) {
-      const double v = p.u_in[q * fstride + gidx];
-      if constexpr (LSRK && !std::is_same<Real, double>::value) u_keep[q] = v;
-      u_s[q * NTILE + t] = to_real<Real>(v);
+      for (int q = 0; q < 9; ++q) cp_async8(&r_s[q * NTILE + t], &p.res[q * fstride + gidx]);
     }
+    cp_async_commit();
+  }
+
+  if (in_tile) {
+    Real w[10], gj[10];
+    if (active) {
 #pragma unroll
-    for (int c = 0; c < 9; ++c) ja[c] = geo[c * fstride + gidx];
-    jinv = geo[9 * fstride + gidx];
-  } else {
+      for (int q = 0; q < 9; ++q) w[q] = to_real<Real>(p.u_in[q * fstride + gidx]);
 #pragma unroll
-    for (int c = 0; c < 9; ++c) ja[c] = 0;
-    if (in_tile) {
+      for (int c = 0; c < 10; ++c) gj[c] = geo[c * fstride + gidx];
+    } else {
 #pragma unroll
-      for (int q = 0; q < 9; ++q) u_s[q * NTILE + t] = 0;
+      for (int c = 0; c < 10; ++c) w[c] = gj[c] = 0;
     }
+    w[9] = 0;
+    V::store10(u_s + t * PK, w);
+    V::store10(g_s + t * PK, gj);
   }
   __syncthreads();
 
@@ -129,14 +198,16 @@ __global__ void __launch_bounds__(Shape<N>::NT) stage_kernel(const StageParams p
 
 #pragma unroll
   for (int dir = 0; dir < 3; ++dir) {
-    const Real m1 = ja[3 * dir + 0], m2 = ja[3 * dir + 1], m3 = ja[3 * dir + 2];
+    Real m1 = 0, m2 = 0, m3 = 0;
     if (in_tile) {
-      Real w[9], F[9];
-#pragma unroll
-      for (int q = 0; q < 9; ++q) w[q] = u_s[q * NTILE + t];
+      m1 = g_s[t * PK + 3 * dir + 0];
+      m2 = g_s[t * PK + 3 * dir + 1];
+      m3 = g_s[t * PK + 3 * dir + 2];
+      Real w[10], F[10];
+      V::load9(u_s + t * PK, w);
       apply_Apos(m1, m2, m3, w, F);
-#pragma unroll
-      for (int q = 0; q < 9; ++q) f_s[q * NTILE + t] = F[q];
+      F[9] = 0;
+      V::store10(f_s + t * PK, F);
     }
     __syncthreads();
     if (in_tile) {
@@ -146,35 +217,37 @@ __global__ void __launch_bounds__(Shape<N>::NT) stage_kernel(const StageParams p
       Real Drow[n];
 #pragma unroll
       for (int b = 0; b < n; ++b) Drow[b] = D_s[a * n + b];
-      Real du[9];
+      Real cs[9], ds[9];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) cs[q] = 0;
+#pragma unroll
+      for (int b = 0; b < n; ++b) {
+        Real F[10];
+        V::load9(f_s + (base + b * stride) * PK, F);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) cs[q] += Drow[b] * F[q];
+      }
 #pragma unroll
       for (int q = 0; q < 9; ++q) {
-        Real cs = 0, ds = 0;
+        acc[q] += cs[q];
+        ds[q] = 0;
+      }
 #pragma unroll
-        for (int b = 0; b < n; ++b) {
-          cs += Drow[b] * f_s[q * NTILE + base + b * stride];
-          ds += Drow[b] * u_s[q * NTILE + base + b * stride];
-        }
-        acc[q] += cs;
-        du[q] = ds;
+      for (int b = 0; b < n; ++b) {
+        Real w[10];
+        V::load9(u_s + (base + b * stride) * PK, w);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) ds[q] += Drow[b] * w[q];
       }
       Real G[9];
-      apply_Apos(m1, m2, m3, du, G);
+      apply_Apos(m1, m2, m3, ds, G);
 #pragma unroll
       for (int q = 0; q < 9; ++q) acc[q] += G[q];
     }
     __syncthreads();
   }
 
-  // Stage the geometry of every node for the face items.
-  if (in_tile) {
-#pragma unroll
-    for (int c = 0; c < 9; ++c) f_s[c * NTILE + t] = ja[c];
-    f_s[9 * NTILE + t] = jinv;
-  }
-  __syncthreads();
-
-  // Face items: lifted flux differences.
+  // Face items: lifted flux differences (x_s now aliases the free flux tile).
   {
     const Real* fz = static_cast<const Real*>(p.fz);
     const Real tau = static_cast<Real>(p.tau);
@@ -196,27 +269,27 @@ __global__ void __launch_bounds__(Shape<N>::NT) stage_kernel(const StageParams p
       const int vn = c0 + n * (c1 + n * c2);
       const int sidx = eli * Np + vn;
 
-      Real du[9];
+      Real um[10], du[9];
+      V::load9(u_s + sidx * PK, um);
       const int g = p.vmapP[static_cast<size_t>(ei) * 6 * nf + r];
       if (g >= 0) {
 #pragma unroll
-        for (int q = 0; q < 9; ++q)
-          du[q] = u_s[q * NTILE + sidx] - to_real<Real>(p.u_in[q * fstride + g]);
+        for (int q = 0; q < 9; ++q) du[q] = um[q] - to_real<Real>(p.u_in[q * fstride + g]);
       } else if (g == kGhostFreeSurface) {
         // exterior (v, -sigma): jump (0, 2 sigma)
 #pragma unroll
         for (int q = 0; q < 3; ++q) du[q] = 0;
 #pragma unroll
-        for (int q = 3; q < 9; ++q) du[q] = 2 * u_s[q * NTILE + sidx];
+        for (int q = 3; q < 9; ++q) du[q] = 2 * um[q];
       } else {
 #pragma unroll
-        for (int q = 0; q < 9; ++q) du[q] = u_s[q * NTILE + sidx];
+        for (int q = 0; q < 9; ++q) du[q] = um[q];
       }
       const Real sgn = hi ? Real(1) : Real(-1);
-      const Real m1 = sgn * f_s[(3 * d + 0) * NTILE + sidx];
-      const Real m2 = sgn * f_s[(3 * d + 1) * NTILE + sidx];
-      const Real m3 = sgn * f_s[(3 * d + 2) * NTILE + sidx];
-      const Real jv = f_s[9 * NTILE + sidx];
+      const Real m1 = sgn * g_s[sidx * PK + 3 * d + 0];
+      const Real m2 = sgn * g_s[sidx * PK + 3 * d + 1];
+      const Real m3 = sgn * g_s[sidx * PK + 3 * d + 2];
+      const Real jv = g_s[sidx * PK + 9];
 
       Real Ad[9];
       apply_Apos(m1, m2, m3, du, Ad);      // A_+(m) du = -A(m) du
@@ -260,7 +333,7 @@ __global__ void __launch_bounds__(Shape<N>::NT) stage_kernel(const StageParams p
 
   // vol = -1/2 (1/J) (-acc_+) = +1/2 (1/J) acc_+  (acc holds A_+ terms)
   Real r[9];
-  const Real hv = static_cast<Real>(0.5) * jinv;
+  const Real hv = static_cast<Real>(0.5) * g_s[t * PK + 9];
 #pragma unroll
   for (int q = 0; q < 9; ++q) r[q] = hv * acc[q];
   const int fb0 = el * 6 * nf;
@@ -305,18 +378,25 @@ __global__ void __launch_bounds__(Shape<N>::NT) stage_kernel(const StageParams p
   } else {
     // res <- a res + dt rhs; u_out <- u_in + b res, both FP64.  a_0 = 0: the
     // incoming register is not read in the first stage.
-    const bool first = p.a == 0.0;
+    if constexpr (kPrefetch) cp_async_wait_all();
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
-      double uq, dtr;
+      const double uq = p.u_in[q * fstride + gidx];     // FP64 state (L2-resident re-read)
+      double dtr;
       if constexpr (std::is_same<Real, double>::value) {
-        uq = u_s[q * NTILE + t];
         dtr = p.dt * rr[q];
       } else {
-        uq = u_keep[q];
         dtr = widen_int(static_cast<float>(p.dt) * rr[q]);
       }
-      const double rn = first ? dtr : fma(p.a, p.res[q * fstride + gidx], dtr);
+      double rin = 0.0;
+      if (!first) {
+        if constexpr (kPrefetch) {
+          rin = r_s[q * NTILE + t];
+        } else {
+          rin = p.res[q * fstride + gidx];
+        }
+      }
+      const double rn = first ? dtr : fma(p.a, rin, dtr);
       p.res[q * fstride + gidx] = rn;
       p.out[q * fstride + gidx] = fma(p.b, rn, uq);
     }
@@ -326,9 +406,12 @@ __global__ void __launch_bounds__(Shape<N>::NT) stage_kernel(const StageParams p
 template <int N, typename Real, bool LSRK>
 cudaError_t launch_stage_t(const StageParams& p, cudaStream_t s) {
   using S = Shape<N>;
-  const size_t smem = sizeof(Real) * (9 * S::NTILE + 10 * S::NTILE + 9 * S::NFACE_ITEMS + S::n * S::n);
+  const size_t smem = StageSmem<N, Real>::bytes;
   cudaError_t err = cudaFuncSetAttribute(stage_kernel<N, Real, LSRK>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  err = cudaFuncSetAttribute(stage_kernel<N, Real, LSRK>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
   if (err != cudaSuccess) return err;
   const long long blocks = (p.nel + S::EPB - 1) / S::EPB;
   if (blocks <= 0) return cudaSuccess;
