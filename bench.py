@@ -48,6 +48,29 @@ def peaks():
     return 6800.0, "fallback"
 
 
+def measured_traffic(precision):
+    """DRAM bytes per stage launch from the committed ncu summary, or None when the
+    stage-kernel sources changed since that capture."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_1711_01175_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in ("dgw_stage.cuh", "dgw_internal.cuh", "dgw_stage_fp64.cu", "dgw_stage_mixed.cu"):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    path = os.path.join(ROOT, "profiles", "stage_kernel_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            k, v = line.split()[:2]
+            vals[k] = v
+    if vals.get("source_sha256") != h.hexdigest()[:16]:
+        return None
+    v = vals.get(f"{precision}_bytes_per_launch")
+    return float(v) if v is not None else None
+
+
 # FP64 peak: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz (nominal 1.26 TFLOP/s).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
@@ -368,7 +391,8 @@ def main():
             flops = algorithmic_flops_per_element(N) * r["nel"]
             ach = flops / (r["stage_ms"] * 1e-3) / 1e12
             r["roofline"] = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                             "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                             "frac": ach / FP64_PEAK_TFLOPS,
+                             "traffic": measured_traffic("fp64") if cfg.E == 64 else None,
                              "kernel": "stage_kernel<4,double,LSRK>",
                              "note": "FP64 flops as written per launch / CUDA-event stage time; peak derived "
                                      "from 152 SMs x 2 DFMA/clk x 2.07 GHz (nominal)"}
@@ -376,7 +400,8 @@ def main():
             nbytes = step_bytes_per_dof(N, 4) * r["dof"] / 5.0      # average per launch
             ach = nbytes / (r["stage_ms"] * 1e-3) / 1e9
             r["roofline"] = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                             "frac": ach / hbm_peak, "traffic": None,
+                             "frac": ach / hbm_peak,
+                             "traffic": measured_traffic("mixed") if cfg.E == 64 else None,
                              "kernel": "stage_kernel<4,float,LSRK>",
                              "note": f"algorithmic bytes {step_bytes_per_dof(N, 4) / 5:.2f} B/DOF per launch "
                                      f"(stage 0: {algorithmic_bytes_per_dof(N, 4, True):.2f}, stages 1-4: "
