@@ -64,7 +64,7 @@ typedef struct {
 } dgw_config;
 
 /* ABI version of this header (bumped on any signature change). */
-#define DGW_ABI_VERSION 1
+#define DGW_ABI_VERSION 2
 int dgw_abi_version(void);
 
 /* GLL nodes r[0..N] (ascending, r[0] = -1, r[N] = +1) and weights w[0..N]
@@ -125,6 +125,14 @@ dgw_status dgw_rhs(dgw_ctx* ctx, const double* u, double* rhs, double t, void* s
  * and written in place.  Device pointers only. */
 dgw_status dgw_stage(dgw_ctx* ctx, const double* u_in, double* u_out, double* res, int stage,
                      double t, double dt, void* stream);
+
+/* dgw_stage followed by the discrete energy of u_out (as dgw_energy, in
+ * FP64), accumulated inside the same kernel from the values it writes, so the
+ * state is not read a second time.  energy_out: host double; synchronises the
+ * stream.  The reduction order differs from dgw_energy's (agreement to
+ * rounding).  DGW_ERR_UNSTABLE if the energy is not finite. */
+dgw_status dgw_stage_energy(dgw_ctx* ctx, const double* u_in, double* u_out, double* res, int stage,
+                            double t, double dt, double* energy_out, void* stream);
 
 /* nsteps LSRK(5,4) steps of size dt from time t0, in place on u and res
  * (res must hold zeros, or the register of the previous step -- its value is

@@ -40,6 +40,7 @@ SIGNATURES = {
     "dgw_material_upload": (_I, [_P, _P, _P, _P]),
     "dgw_rhs": (_I, [_P, _P, _P, _D, _P]),
     "dgw_stage": (_I, [_P, _P, _P, _P, _I, _D, _D, _P]),
+    "dgw_stage_energy": (_I, [_P, _P, _P, _P, _I, _D, _D, ctypes.POINTER(_D), _P]),
     "dgw_step": (_I, [_P, _P, _P, _D, _D, _I, _P]),
     "dgw_energy": (_I, [_P, _P, ctypes.POINTER(_D), _P]),
     "dgw_adjoint_step": (_I, [_P, _P, _P, _P, _P, _D, _D, _I, _P]),
@@ -114,6 +115,12 @@ def dgw_rhs(ctx, u, rhs, t, stream):
 
 def dgw_stage(ctx, u_in, u_out, res, stage, t, dt, stream):
     return load().dgw_stage(ctx, u_in, u_out, res, stage, t, dt, stream)
+
+
+def dgw_stage_energy(ctx, u_in, u_out, res, stage, t, dt, stream):
+    out = _D()
+    st = load().dgw_stage_energy(ctx, u_in, u_out, res, stage, t, dt, ctypes.byref(out), stream)
+    return st, out.value
 
 
 def dgw_step(ctx, u, res, t0, dt, nsteps, stream):

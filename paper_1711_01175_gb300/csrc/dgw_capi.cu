@@ -57,6 +57,8 @@ void free_mesh(dgw_ctx* c) {
   dfree(c->wJ);
   dfree(c->u2);
   dfree(c->partials);
+  dfree(c->stage_partials);
+  c->stage_ctas = 0;
   dfree(c->stage_u);
   dfree(c->stage_res);
   dfree(c->mat);
@@ -77,8 +79,11 @@ bool is_device_ptr(const void* p) {
 int Np_of(int N) { return (N + 1) * (N + 1) * (N + 1); }
 
 dgw_status launch_stage(dgw_ctx* c, const double* u_in, double* out, double* res, bool lsrk,
-                        double a, double b, double dt, cudaStream_t s) {
+                        double a, double b, double dt, cudaStream_t s, double* energy_partials = nullptr) {
   dgw::StageParams p{};
+  p.energy_partials = energy_partials;
+  p.wJ = c->wJ;
+  p.ec = c->ec;
   p.u_in = u_in;
   p.out = out;
   p.res = res;
@@ -355,6 +360,12 @@ dgw_status dgw_mesh_upload(dgw_ctx* c, int64_t nel, const double* x, const int64
   DGW_TRY(cudaMalloc(&c->vmapP, fnodes * sizeof(int)), "alloc neighbour map");
   DGW_TRY(cudaMalloc(&c->u2, nodes * 9 * sizeof(double)), "alloc state buffer");
   DGW_TRY(cudaMalloc(&c->partials, (dgw::kEnergyBlocks + 1) * sizeof(double)), "alloc energy partials");
+  {
+    int epb = 0, nthreads = 0;
+    dgw::stage_shape(N, &epb, &nthreads);
+    c->stage_ctas = (int)((nel + epb - 1) / epb);
+    DGW_TRY(cudaMalloc(&c->stage_partials, ((size_t)c->stage_ctas + 1) * sizeof(double)), "alloc stage energy partials");
+  }
   DGW_TRY(cudaMemcpy(x_d, x, nodes * 3 * sizeof(double), cudaMemcpyHostToDevice), "copy x");
   DGW_TRY(cudaMemcpy(D_d, c->ref.D, sizeof(c->ref.D), cudaMemcpyHostToDevice), "copy D");
   DGW_TRY(cudaMemcpy(w_d, c->ref.w, sizeof(c->ref.w), cudaMemcpyHostToDevice), "copy w");
@@ -490,6 +501,31 @@ dgw_status dgw_stage(dgw_ctx* c, const double* u_in, double* u_out, double* res,
     return fail(c, DGW_ERR_ARG, "dgw_stage takes device pointers");
   if (set_device(c) != DGW_OK) return DGW_ERR_CUDA;
   return launch_stage(c, u_in, u_out, res, true, kLsrkA[stage], kLsrkB[stage], dt, (cudaStream_t)stream);
+}
+
+dgw_status dgw_stage_energy(dgw_ctx* c, const double* u_in, double* u_out, double* res, int stage, double t,
+                            double dt, double* energy_out, void* stream) {
+  (void)t;
+  dgw_status st = ready(c);
+  if (st != DGW_OK) return st;
+  if (stage < 0 || stage > 4) return fail(c, DGW_ERR_ARG, "stage %d outside 0..4", stage);
+  if (!energy_out) return fail(c, DGW_ERR_ARG, "null energy_out");
+  if (!u_in || !u_out || !res || (const void*)u_in == (void*)u_out || (void*)u_out == (void*)res ||
+      (const void*)u_in == (void*)res)
+    return fail(c, DGW_ERR_ARG, "u_in, u_out and res must be distinct non-null buffers");
+  if (!is_device_ptr(u_in) || !is_device_ptr(u_out) || !is_device_ptr(res))
+    return fail(c, DGW_ERR_ARG, "dgw_stage_energy takes device pointers");
+  if (set_device(c) != DGW_OK) return DGW_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = launch_stage(c, u_in, u_out, res, true, kLsrkA[stage], kLsrkB[stage], dt, s, c->stage_partials)) != DGW_OK)
+    return st;
+  double* result = c->stage_partials + c->stage_ctas;
+  DGW_CUDA(c, dgw::launch_energy_final(c->stage_partials, c->stage_ctas, result, s), "energy reduction");
+  DGW_CUDA(c, cudaMemcpyAsync(c->pinned, result, sizeof(double), cudaMemcpyDeviceToHost, s), "copy energy");
+  DGW_CUDA(c, cudaStreamSynchronize(s), "stage energy");
+  *energy_out = *c->pinned;
+  if (!std::isfinite(*energy_out)) return fail(c, DGW_ERR_UNSTABLE, "energy is not finite");
+  return DGW_OK;
 }
 
 dgw_status dgw_step(dgw_ctx* c, double* u, double* res, double t0, double dt, int nsteps, void* stream) {

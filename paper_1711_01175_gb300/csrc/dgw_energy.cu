@@ -78,4 +78,9 @@ cudaError_t launch_energy(const double* u, const double* wJ, const double* ec, l
   return cudaGetLastError();
 }
 
+cudaError_t launch_energy_final(const double* partials, int nparts, double* result, cudaStream_t s) {
+  energy_final_kernel<<<1, kEnergyThreads, 0, s>>>(partials, nparts, result);
+  return cudaGetLastError();
+}
+
 }  // namespace dgw

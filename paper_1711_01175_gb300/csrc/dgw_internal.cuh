@@ -30,7 +30,7 @@ struct Shape {
   static constexpr int n = N + 1;
   static constexpr int Np = n * n * n;
   static constexpr int nf = n * n;
-  static constexpr int EPB = (N == 1) ? 16 : (N == 2) ? 9 : (N == 3) ? 4 : (N == 4) ? 2 : 1;
+  static constexpr int EPB = (N == 1) ? 16 : (N == 2) ? 9 : (N == 3) ? 4 : 1;
   static constexpr int NTILE = EPB * Np;
   static constexpr int NT = ((NTILE + 31) / 32) * 32;
   static constexpr int NFACE_ITEMS = EPB * 6 * nf;
@@ -54,6 +54,9 @@ struct StageParams {
   double a, b, dt;        // LSRK coefficients of this stage and the step size
   double tau;             // 0 central, 1 upwind
   double w_end_inv;       // 1 / w_0 (GLL end weight)
+  double* energy_partials;  // LSRK mode, optional: one partial sum of w J u_out^T Q u_out per CTA
+  const double* wJ;         // [nel][Np] (with energy_partials)
+  const double* ec;         // [4][nel] energy constants (with energy_partials)
   double D[(kMaxN + 1) * (kMaxN + 1)];
 };
 
@@ -77,6 +80,7 @@ constexpr int kEnergyBlocks = 152 * 4;
 constexpr int kEnergyThreads = 256;
 cudaError_t launch_energy(const double* u, const double* wJ, const double* ec, long long nel, int Np,
                           double* partials, double* result, cudaStream_t s);
+cudaError_t launch_energy_final(const double* partials, int nparts, double* result, cudaStream_t s);
 
 // Message storage of calls without a context (read by dgw_last_error(NULL)).
 void set_no_context_error(const std::string& msg);
@@ -99,6 +103,8 @@ struct dgw_ctx {
   double* wJ = nullptr;      // [nel][Np]
   double* u2 = nullptr;      // second state buffer for the stage ping-pong
   double* partials = nullptr;  // energy partial sums + result slot
+  double* stage_partials = nullptr;  // per-CTA energy partials of a fused stage + result slot
+  int stage_ctas = 0;
   double* stage_u = nullptr;   // host-pointer staging buffers
   double* stage_res = nullptr;
   double* pinned = nullptr;    // pinned host slot for the energy value

@@ -127,7 +127,8 @@ struct StageSmem {
   static constexpr size_t fbytes = sizeof(Real) * (S::NTILE * PK > 9 * S::NFACE_ITEMS ? S::NTILE * PK : 9 * S::NFACE_ITEMS);
   static constexpr size_t g_off = f_off + ((fbytes + 15) / 16) * 16;     // Real [NTILE][PK] Ja, 1/J
   static constexpr size_t d_off = g_off + sizeof(Real) * S::NTILE * PK;  // Real [n*n]
-  static constexpr size_t r_off = ((d_off + sizeof(Real) * S::n * S::n + 15) / 16) * 16;  // double [9][NTILE]
+  static constexpr size_t e_off = ((d_off + sizeof(Real) * S::n * S::n + 15) / 16) * 16;  // double [32] reduction
+  static constexpr size_t r_off = e_off + sizeof(double) * 32;                            // double [9][NTILE]
   static constexpr size_t bytes = r_off + (kPrefetchRes ? sizeof(double) * 9 * S::NTILE : 0);
 };
 
@@ -147,6 +148,7 @@ __global__ void __launch_bounds__(Shape<N>::NT) stage_kernel(const StageParams p
   Real* g_s = reinterpret_cast<Real*>(smem_raw + L::g_off);
   Real* D_s = reinterpret_cast<Real*>(smem_raw + L::d_off);
   double* r_s = reinterpret_cast<double*>(smem_raw + L::r_off);
+  double* red_s = reinterpret_cast<double*>(smem_raw + L::e_off);
 
   const int t = threadIdx.x;
   for (int i = t; i < n * n; i += NT) D_s[i] = static_cast<Real>(p.D[i]);
@@ -329,76 +331,102 @@ __global__ void __launch_bounds__(Shape<N>::NT) stage_kernel(const StageParams p
   }
   __syncthreads();
 
-  if (!active) return;
+  double e_node = 0.0;     // w J u_out^T Q u_out of this node (fused energy)
+  if (active) {
+    // vol = -1/2 (1/J) (-acc_+) = +1/2 (1/J) acc_+  (acc holds A_+ terms)
+    Real r[9];
+    const Real hv = static_cast<Real>(0.5) * g_s[t * PK + 9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) r[q] = hv * acc[q];
+    const int fb0 = el * 6 * nf;
+    auto add_face = [&](int f, int pidx) {
+#pragma unroll
+      for (int q = 0; q < 9; ++q) r[q] += x_s[q * NFI + fb0 + f * nf + pidx];
+    };
+    if (ix == 0) add_face(0, iy + n * iz);
+    if (ix == N) add_face(1, iy + n * iz);
+    if (iy == 0) add_face(2, ix + n * iz);
+    if (iy == N) add_face(3, ix + n * iz);
+    if (iz == 0) add_face(4, ix + n * iy);
+    if (iz == N) add_face(5, ix + n * iy);
 
-  // vol = -1/2 (1/J) (-acc_+) = +1/2 (1/J) acc_+  (acc holds A_+ terms)
-  Real r[9];
-  const Real hv = static_cast<Real>(0.5) * g_s[t * PK + 9];
-#pragma unroll
-  for (int q = 0; q < 9; ++q) r[q] = hv * acc[q];
-  const int fb0 = el * 6 * nf;
-  auto add_face = [&](int f, int pidx) {
-#pragma unroll
-    for (int q = 0; q < 9; ++q) r[q] += x_s[q * NFI + fb0 + f * nf + pidx];
-  };
-  if (ix == 0) add_face(0, iy + n * iz);
-  if (ix == N) add_face(1, iy + n * iz);
-  if (iy == 0) add_face(2, ix + n * iz);
-  if (iy == N) add_face(3, ix + n * iz);
-  if (iz == 0) add_face(4, ix + n * iy);
-  if (iz == N) add_face(5, ix + n * iy);
+    // Q^{-1}: velocity rows / rho, stress rows by the isotropic stiffness C_V.
+    const Real* mat = static_cast<const Real*>(p.mat);
+    const Real irho = mat[e];
+    const Real lam = mat[p.nel + e];
+    const Real mu = mat[2 * p.nel + e];
+    Real rr[9];
+    rr[0] = irho * r[0];
+    rr[1] = irho * r[1];
+    rr[2] = irho * r[2];
+    const Real tr = r[3] + r[4] + r[5];
+    const Real two_mu = mu + mu;
+    rr[3] = lam * tr + two_mu * r[3];
+    rr[4] = lam * tr + two_mu * r[4];
+    rr[5] = lam * tr + two_mu * r[5];
+    rr[6] = mu * r[6];
+    rr[7] = mu * r[7];
+    rr[8] = mu * r[8];
 
-  // Q^{-1}: velocity rows / rho, stress rows by the isotropic stiffness C_V.
-  const Real* mat = static_cast<const Real*>(p.mat);
-  const Real irho = mat[e];
-  const Real lam = mat[p.nel + e];
-  const Real mu = mat[2 * p.nel + e];
-  Real rr[9];
-  rr[0] = irho * r[0];
-  rr[1] = irho * r[1];
-  rr[2] = irho * r[2];
-  const Real tr = r[3] + r[4] + r[5];
-  const Real two_mu = mu + mu;
-  rr[3] = lam * tr + two_mu * r[3];
-  rr[4] = lam * tr + two_mu * r[4];
-  rr[5] = lam * tr + two_mu * r[5];
-  rr[6] = mu * r[6];
-  rr[7] = mu * r[7];
-  rr[8] = mu * r[8];
-
-  if constexpr (!LSRK) {
+    if constexpr (!LSRK) {
 #pragma unroll
-    for (int q = 0; q < 9; ++q) {
-      if constexpr (std::is_same<Real, double>::value) {
-        p.out[q * fstride + gidx] = rr[q];
-      } else {
-        p.out[q * fstride + gidx] = widen_int(rr[q]);
-      }
-    }
-  } else {
-    // res <- a res + dt rhs; u_out <- u_in + b res, both FP64.  a_0 = 0: the
-    // incoming register is not read in the first stage.
-    if constexpr (kPrefetch) cp_async_wait_all();
-#pragma unroll
-    for (int q = 0; q < 9; ++q) {
-      const double uq = p.u_in[q * fstride + gidx];     // FP64 state (L2-resident re-read)
-      double dtr;
-      if constexpr (std::is_same<Real, double>::value) {
-        dtr = p.dt * rr[q];
-      } else {
-        dtr = widen_int(static_cast<float>(p.dt) * rr[q]);
-      }
-      double rin = 0.0;
-      if (!first) {
-        if constexpr (kPrefetch) {
-          rin = r_s[q * NTILE + t];
+      for (int q = 0; q < 9; ++q) {
+        if constexpr (std::is_same<Real, double>::value) {
+          p.out[q * fstride + gidx] = rr[q];
         } else {
-          rin = p.res[q * fstride + gidx];
+          p.out[q * fstride + gidx] = widen_int(rr[q]);
         }
       }
-      const double rn = first ? dtr : fma(p.a, rin, dtr);
-      p.res[q * fstride + gidx] = rn;
-      p.out[q * fstride + gidx] = fma(p.b, rn, uq);
+    } else {
+      // res <- a res + dt rhs; u_out <- u_in + b res, both FP64.  a_0 = 0: the
+      // incoming register is not read in the first stage.
+      if constexpr (kPrefetch) cp_async_wait_all();
+      double uout[9];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) {
+        const double uq = p.u_in[q * fstride + gidx];     // FP64 state (L2-resident re-read)
+        double dtr;
+        if constexpr (std::is_same<Real, double>::value) {
+          dtr = p.dt * rr[q];
+        } else {
+          dtr = widen_int(static_cast<float>(p.dt) * rr[q]);
+        }
+        double rin = 0.0;
+        if (!first) {
+          if constexpr (kPrefetch) {
+            rin = r_s[q * NTILE + t];
+          } else {
+            rin = p.res[q * fstride + gidx];
+          }
+        }
+        const double rn = first ? dtr : fma(p.a, rin, dtr);
+        p.res[q * fstride + gidx] = rn;
+        const double uo = fma(p.b, rn, uq);
+        p.out[q * fstride + gidx] = uo;
+        uout[q] = uo;
+      }
+      if (p.energy_partials != nullptr) {
+        const double rho = p.ec[e], i2mu = p.ec[p.nel + e], lfac = p.ec[2 * p.nel + e], imu = p.ec[3 * p.nel + e];
+        const double tr2 = uout[3] + uout[4] + uout[5];
+        const double kin = rho * (uout[0] * uout[0] + uout[1] * uout[1] + uout[2] * uout[2]);
+        const double pot = i2mu * (uout[3] * uout[3] + uout[4] * uout[4] + uout[5] * uout[5] - lfac * tr2 * tr2) +
+                           imu * (uout[6] * uout[6] + uout[7] * uout[7] + uout[8] * uout[8]);
+        e_node = p.wJ[gidx] * (kin + pot);
+      }
+    }
+  }
+  if constexpr (LSRK) {
+    if (p.energy_partials != nullptr) {
+      // Block sum of the node energies in a fixed order (bit-reproducible).
+      double v = e_node;
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+      if ((t & 31) == 0) red_s[t >> 5] = v;
+      __syncthreads();
+      if (t < 32) {
+        double w2 = t < NT / 32 ? red_s[t] : 0.0;
+        for (int off = 16; off > 0; off >>= 1) w2 += __shfl_down_sync(0xffffffffu, w2, off);
+        if (t == 0) p.energy_partials[blockIdx.x] = w2;
+      }
     }
   }
 }

@@ -110,6 +110,15 @@ class Solver:
         self._check(capi.dgw_stage(self._ctx, _ptr(u_in), _ptr(u_out), _ptr(res), int(s), float(t),
                                    float(dt), _stream_handle(stream)))
 
+    def stage_energy(self, u_in, u_out, res, s: int, dt: float, t: float = 0.0, stream=None) -> float:
+        """dgw_stage plus the energy of u_out, fused into the same kernel."""
+        for a, nm in ((u_in, "u_in"), (u_out, "u_out"), (res, "res")):
+            self._field_check(a, nm)
+        st, val = capi.dgw_stage_energy(self._ctx, _ptr(u_in), _ptr(u_out), _ptr(res), int(s), float(t),
+                                        float(dt), _stream_handle(stream))
+        self._check(st)
+        return val
+
     def step(self, u, res, dt: float, nsteps: int = 1, t0: float = 0.0, stream=None):
         self._field_check(u, "u")
         self._field_check(res, "res")

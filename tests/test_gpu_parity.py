@@ -138,6 +138,29 @@ def test_energy_parity_and_decay():
         prev = e
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_fused_stage_energy_matches_separate_calls(precision):
+    """dgw_stage_energy writes the same stage output as dgw_stage and returns the
+    energy of u_out as dgw_energy computes it (different summation order)."""
+    import torch
+    cfg = wl.large_config(E=6)
+    c = Case(cfg.E, cfg.N, cfg.amplitude, cfg.periodic, cfg.boundary, cfg.order, material=1,
+             initial="gaussian_pulse", precision=precision)
+    dt = c.solver.dt_cfl()
+    for s in (0, 3):
+        u = torch_cuda(c.u0)
+        res0 = torch_cuda(wl.random_state(c.mesh.nel, 125, 5 + s)) * 1e-3
+        out_a, out_b = torch.empty_like(u), torch.empty_like(u)
+        res_a, res_b = res0.clone(), res0.clone()
+        c.solver.stage(u, out_a, res_a, s, dt)
+        e = c.solver.stage_energy(u, out_b, res_b, s, dt)
+        assert torch.equal(out_a, out_b) and torch.equal(res_a, res_b)
+        e_ref = c.solver.energy(out_b)
+        assert abs(e - e_ref) <= 1e-13 * e_ref
+        if precision == "fp64":
+            assert abs(e - c.op.energy(out_b.cpu().numpy())) <= 1e-13 * e_ref
+
+
 def test_host_pointer_paths_match_device_paths():
     import torch
     c = Case(3, 4, 0.1, material=2, seed=8)
