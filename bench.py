@@ -150,8 +150,15 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
-def build_workload(E, N):
-    cfg = wl.large_config(E=E, N=N)
+def workload_config(name, E=None):
+    if name == "precision":
+        return wl.precision_config(E=E or 48)
+    return wl.large_config(E=E or 64)
+
+
+def build_workload(name, E=None):
+    cfg = workload_config(name, E)
+    N = cfg.N
     from paper_1711_01175_gb300 import reference_nodes
     r, _ = reference_nodes(N)
     data = cfg.build(r)
@@ -290,8 +297,8 @@ def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    E, N = args.elements, 4
-    cfg, data = build_workload_oracle(E, N)
+    cfg, data = build_workload_oracle(args.workload, args.elements)
+    N = cfg.N
     per_step = []
     total_units = 0
     import oracle
@@ -318,7 +325,7 @@ def reference_arm(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": cfg.name, "elements": m.nel, "N": N,
+            "config": {"workload": cfg.name, "elements": m.nel, "N": N, "precision": "fp64",
                        "sample_elements": len(elems)},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"one LSRK step (5 stages) per bench step on {len(elems)} of "
@@ -327,10 +334,10 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
-def build_workload_oracle(E, N):
+def build_workload_oracle(name, E=None):
     import oracle
-    cfg = wl.large_config(E=E, N=N)
-    r, _ = oracle.gll(N)
+    cfg = workload_config(name, E)
+    r, _ = oracle.gll(cfg.N)
     return cfg, cfg.build(r)
 
 
@@ -341,7 +348,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--precision", default="both", choices=["both", "fp64", "mixed"])
-    ap.add_argument("--elements", type=int, default=64, help="elements per axis (64: the large workload)")
+    ap.add_argument("--workload", default="large", choices=["large", "precision"],
+                    help="large: 64^3, N=4 (the metric's workload); precision: 48^3, N=7")
+    ap.add_argument("--elements", type=int, default=None, help="elements per axis (default: the workload's)")
     ap.add_argument("--mixed-steps", type=int, default=None, help="steps for the mixed variant (default 4x)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -371,7 +380,7 @@ def main():
         torch.distributed.barrier()
     g.build()
 
-    cfg, data = build_workload(args.elements, 4)
+    cfg, data = build_workload(args.workload, args.elements)
     hbm_peak, peak_kind = peaks()
     variants = ["fp64", "mixed"] if args.precision == "both" else [args.precision]
     results = {}
@@ -398,8 +407,8 @@ def main():
             ach = flops / (r["stage_ms"] * 1e-3) / 1e12
             r["roofline"] = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                              "frac": ach / FP64_PEAK_TFLOPS,
-                             "traffic": measured_traffic("fp64") if cfg.E == 64 else None,
-                             "kernel": "stage_kernel<4,double,LSRK>",
+                             "traffic": measured_traffic("fp64") if cfg.name == "large-64^3-N4" else None,
+                             "kernel": f"stage_kernel<{N},double,LSRK>",
                              "note": "FP64 flops as written per launch / CUDA-event stage time; peak derived "
                                      "from 152 SMs x 2 DFMA/clk x 2.07 GHz (nominal)"}
         else:
@@ -407,8 +416,8 @@ def main():
             ach = nbytes / (r["stage_ms"] * 1e-3) / 1e9
             r["roofline"] = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
                              "frac": ach / hbm_peak,
-                             "traffic": measured_traffic("mixed") if cfg.E == 64 else None,
-                             "kernel": "stage_kernel<4,float,LSRK>",
+                             "traffic": measured_traffic("mixed") if cfg.name == "large-64^3-N4" else None,
+                             "kernel": f"stage_kernel<{N},float,LSRK>",
                              "note": f"algorithmic bytes {step_bytes_per_dof(N, 4) / 5:.2f} B/DOF per launch "
                                      f"(stage 0: {algorithmic_bytes_per_dof(N, 4, True):.2f}, stages 1-4: "
                                      f"{algorithmic_bytes_per_dof(N, 4):.2f}); peak {peak_kind} copy bandwidth"}

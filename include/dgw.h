@@ -64,7 +64,7 @@ typedef struct {
 } dgw_config;
 
 /* ABI version of this header (bumped on any signature change). */
-#define DGW_ABI_VERSION 2
+#define DGW_ABI_VERSION 3
 int dgw_abi_version(void);
 
 /* GLL nodes r[0..N] (ascending, r[0] = -1, r[N] = +1) and weights w[0..N]
@@ -146,6 +146,18 @@ dgw_status dgw_step(dgw_ctx* ctx, double* u, double* res, double t0, double dt, 
  * energy_out: host double.  Synchronises the stream.  DGW_ERR_UNSTABLE if E
  * is not finite (the value is still written). */
 dgw_status dgw_energy(dgw_ctx* ctx, const double* u, double* energy_out, void* stream);
+
+/* Point force F R(t) delta(x - x_s) in the velocity equations (the forcing f
+ * of eq. LPDE): x_s is the image of the reference point xi[3] (in [-1,1]^3)
+ * of `element`, F = force[3], and R is the Ricker wavelet
+ * (1 - 2 (pi f0 (t - t0))^2) exp(-(pi f0 (t - t0))^2).  It is projected by
+ * collocation, F R(t) l_j(xi) / (w_j J_j), added to the right-hand side of
+ * that element at the stage times t + c_s dt of dgw_rhs/dgw_stage/dgw_step
+ * (whose t arguments are the step start times).  element = -1 removes the
+ * source.  DGW_ERR_STATE before mesh and material (material sets rho of the
+ * source element: upload material first, set the source after). */
+dgw_status dgw_source_set(dgw_ctx* ctx, int64_t element, const double* xi, const double* force, double f0,
+                          double t0);
 
 /* Adjoint of dgw_step with material gradients.  Not built yet: returns
  * DGW_ERR_UNSUPPORTED. */

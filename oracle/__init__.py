@@ -7,4 +7,4 @@ library never imports it.
 from .dg_elastic import (ElasticDG, gll, lagrange_derivative_matrix, legendre, A_of, B_of, abs_A, abs_A_Q,
                          Q_of, stiffness_voigt, weighted_trace, hdg_flux, LSRK_A, LSRK_B, LSRK_C,
                          cfl_dt, cfl_number, face_node_indices, neighbour_face_position,
-                         h_min_corner_edges)
+                         h_min_corner_edges, ricker, lagrange_values)

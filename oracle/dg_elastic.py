@@ -208,6 +208,23 @@ LSRK_C = [Fraction(0), Fraction(1432997174477, 9575080441755),
           Fraction(2802321613138, 2924317926251)]
 
 
+def ricker(t, f0, t0):
+    """Ricker wavelet (1 - 2 (pi f0 (t - t0))^2) exp(-(pi f0 (t - t0))^2)."""
+    a = (np.pi * f0 * (np.asarray(t, dtype=np.float64) - t0)) ** 2
+    return (1.0 - 2.0 * a) * np.exp(-a)
+
+
+def lagrange_values(r, xi):
+    """l_j(xi) for the Lagrange basis on nodes r (product formula)."""
+    r = np.asarray(r, dtype=np.float64)
+    out = np.ones(r.size)
+    for j in range(r.size):
+        for k in range(r.size):
+            if k != j:
+                out[j] *= (xi - r[k]) / (r[j] - r[k])
+    return out
+
+
 def cfl_dt(cfl, h, c_max, N):
     """dt = CFL h / (c_max N^2): the CFL number CFL = dt |beta| p^2 / h that the
     paper's time-dependent transport table lists (Section 6.1)."""
@@ -269,6 +286,7 @@ class ElasticDG:
         wv = np.einsum("k,j,i->kji", self.w, self.w, self.w).ravel()
         self.w_vol = wv                                        # [Np]
         self.w_face = np.einsum("b,a->ba", self.w, self.w).ravel()   # [n^2], a fastest
+        self.source = None
         self._geo_cache = {}
         self._nbr_cache = {}
         self._abs_cache = {}
@@ -415,8 +433,26 @@ class ElasticDG:
             out[:, :, fn] += np.moveaxis(q * scale[..., None], -1, 0)
         return out
 
-    def rhs(self, u, elems=None):
-        """L(u) = Q^{-1}[volume + surface] for the elements in elems (default all)."""
+    def set_point_force(self, element, xi, force, f0, t0):
+        """Point force F R(t) delta(x - x_s) in the velocity equations (the forcing f
+        of eq. LPDE), x_s the image of reference point xi in `element`, R a Ricker
+        wavelet of peak frequency f0 centred at t0."""
+        self.source = (int(element), np.asarray(xi, dtype=np.float64), np.asarray(force, dtype=np.float64),
+                       float(f0), float(t0))
+
+    def source_nodal(self, t):
+        """Collocation projection of the point force: M^{-1} int f phi_j, i.e.
+        F R(t) l_j(xi_s) / (w_j J_j) at the nodes of the source element (before Q^{-1})."""
+        e, xi, F, f0, t0 = self.source
+        li = [lagrange_values(self.r, xi[a]) for a in range(3)]
+        l3 = np.einsum("k,j,i->kji", li[2], li[1], li[0]).ravel()
+        _, J = self.geometry(np.array([e]))
+        s = np.zeros((NFIELD, self.Np))
+        s[:3] = F[:, None] * float(ricker(t, f0, t0)) * l3[None, :] / (self.w_vol * J[0])[None, :]
+        return e, s
+
+    def rhs(self, u, elems=None, t=0.0):
+        """L(u) = Q^{-1}[volume + surface + source] for the elements in elems (default all)."""
         u = np.asarray(u, dtype=np.float64)
         elems = np.arange(self.nel) if elems is None else np.asarray(elems, dtype=np.int64)
         Ja, J = self.geometry(elems)
@@ -424,22 +460,28 @@ class ElasticDG:
             raise ValueError("non-positive Jacobian")
         u_e = u[:, elems]
         r = self.volume_term(u_e, Ja, J) + self.surface_term(u, elems, Ja, J)
+        if self.source is not None:
+            es, sn = self.source_nodal(t)
+            hit = np.nonzero(elems == es)[0]
+            if hit.size:
+                r[:, hit[0]] += sn
         return np.einsum("epq,qen->pen", self.Qinv(elems), r)
 
     # ---- time stepping ---------------------------------------------------
-    def lsrk_stage(self, u, res, s, dt, elems=None):
-        """One 2N-storage stage: res <- a_s res + dt L(u); u <- u + b_s res."""
+    def lsrk_stage(self, u, res, s, dt, elems=None, t=0.0):
+        """One 2N-storage stage from step time t: res <- a_s res + dt L(u, t + c_s dt);
+        u <- u + b_s res."""
         elems = np.arange(self.nel) if elems is None else np.asarray(elems, dtype=np.int64)
         a, b = float(LSRK_A[s]), float(LSRK_B[s])
-        res_new = a * res[:, elems] + dt * self.rhs(u, elems)
+        res_new = a * res[:, elems] + dt * self.rhs(u, elems, t + float(LSRK_C[s]) * dt)
         u_new = u[:, elems] + b * res_new
         return u_new, res_new
 
-    def step(self, u, res, dt):
+    def step(self, u, res, dt, t=0.0):
         u = u.copy()
         res = res.copy()
         for s in range(5):
-            u, res = self.lsrk_stage(u, res, s, dt)
+            u, res = self.lsrk_stage(u, res, s, dt, t=t)
         return u, res
 
     # ---- energy -----------------------------------------------------------

@@ -43,6 +43,7 @@ SIGNATURES = {
     "dgw_stage_energy": (_I, [_P, _P, _P, _P, _I, _D, _D, ctypes.POINTER(_D), _P]),
     "dgw_step": (_I, [_P, _P, _P, _D, _D, _I, _P]),
     "dgw_energy": (_I, [_P, _P, ctypes.POINTER(_D), _P]),
+    "dgw_source_set": (_I, [_P, _I64, _P, _P, _D, _D]),
     "dgw_adjoint_step": (_I, [_P, _P, _P, _P, _P, _D, _D, _I, _P]),
     "dgw_dt_cfl": (_I, [_P, ctypes.POINTER(_D)]),
     "dgw_energy_static": (_I, [_I, _I64, _P, _P, _P, _P, _P, _P, _P]),
@@ -131,6 +132,10 @@ def dgw_energy(ctx, u, stream):
     out = _D()
     st = load().dgw_energy(ctx, u, ctypes.byref(out), stream)
     return st, out.value
+
+
+def dgw_source_set(ctx, element, xi, force, f0, t0):
+    return load().dgw_source_set(ctx, element, xi, force, f0, t0)
 
 
 def dgw_adjoint_step(ctx, lam_u, lam_res, grad_mat, u_ckpt, t0, dt, nsteps, stream):

@@ -40,6 +40,8 @@ dgw_status cuda_fail(dgw_ctx* ctx, cudaError_t e, const char* what) {
 // LSRK(5,4) of Carpenter & Kennedy (1994), 2N-storage, five stages, fourth order.
 const double kLsrkA[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
                           -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
+const double kLsrkC[5] = {0.0, 1432997174477.0 / 9575080441755.0, 2526269341429.0 / 6820363962896.0,
+                          2006345519317.0 / 3224310063776.0, 2802321613138.0 / 2924317926251.0};
 const double kLsrkB[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
                           1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
                           2277821191437.0 / 14882151754819.0};
@@ -63,6 +65,8 @@ void free_mesh(dgw_ctx* c) {
   dfree(c->stage_res);
   dfree(c->mat);
   dfree(c->ec);
+  dfree(c->src_w);
+  c->src_elem = -1;
   c->has_mesh = c->has_material = false;
   c->nel = 0;
 }
@@ -78,9 +82,24 @@ bool is_device_ptr(const void* p) {
 
 int Np_of(int N) { return (N + 1) * (N + 1) * (N + 1); }
 
+// Ricker wavelet (1 - 2 (pi f0 (t - t0))^2) exp(-(pi f0 (t - t0))^2).
+double ricker(double t, double f0, double t0) {
+  const double a = M_PI * f0 * (t - t0);
+  return (1.0 - 2.0 * a * a) * std::exp(-a * a);
+}
+
 dgw_status launch_stage(dgw_ctx* c, const double* u_in, double* out, double* res, bool lsrk,
-                        double a, double b, double dt, cudaStream_t s, double* energy_partials = nullptr) {
+                        double a, double b, double dt, cudaStream_t s, double* energy_partials = nullptr,
+                        double t_stage = 0.0) {
   dgw::StageParams p{};
+  {
+    int epb = 0, nthreads = 0;
+    dgw::stage_shape(c->cfg.N, &epb, &nthreads);
+    p.pf_elems = 2LL * c->sm_count * epb;
+  }
+  p.src_elem = c->src_elem;
+  p.src_w = c->src_w;
+  p.src_amp = c->src_elem >= 0 ? ricker(t_stage, c->src_f0, c->src_t0) : 0.0;
   p.energy_partials = energy_partials;
   p.wJ = c->wJ;
   p.ec = c->ec;
@@ -229,6 +248,7 @@ dgw_status dgw_create(dgw_ctx** out, int device, const dgw_config* cfg) {
     delete c;
     return fail(nullptr, DGW_ERR_CUDA, "cudaSetDevice(%d) failed", device);
   }
+  cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
   if (cudaMallocHost((void**)&c->pinned, sizeof(double)) != cudaSuccess) {
     delete c;
     return fail(nullptr, DGW_ERR_OOM, "pinned host slot");
@@ -442,6 +462,8 @@ dgw_status dgw_material_upload(dgw_ctx* c, const double* rho, const double* lam,
   dfree(c->mat);
   dfree(c->ec);
   dfree(c->fz);
+  dfree(c->src_w);          // the source weights depend on rho: set the source again
+  c->src_elem = -1;
   c->has_material = false;
   DGW_CUDA(c, cudaMalloc(&c->ec, 4 * nel * sizeof(double)), "alloc energy constants");
   DGW_CUDA(c, cudaMemcpy(c->ec, ec.data(), 4 * nel * sizeof(double), cudaMemcpyHostToDevice), "copy energy constants");
@@ -471,7 +493,6 @@ static dgw_status ensure_staging(dgw_ctx* c, bool need_res) {
 }
 
 dgw_status dgw_rhs(dgw_ctx* c, const double* u, double* rhs, double t, void* stream) {
-  (void)t;
   dgw_status st = ready(c);
   if (st != DGW_OK) return st;
   if (!u || !rhs || (const void*)u == (void*)rhs) return fail(c, DGW_ERR_ARG, "u and rhs must be distinct non-null buffers");
@@ -479,10 +500,10 @@ dgw_status dgw_rhs(dgw_ctx* c, const double* u, double* rhs, double t, void* str
   cudaStream_t s = (cudaStream_t)stream;
   const size_t bytes = (size_t)c->nel * Np_of(c->cfg.N) * 9 * sizeof(double);
   const bool host = !is_device_ptr(u) || !is_device_ptr(rhs);
-  if (!host) return launch_stage(c, u, rhs, nullptr, false, 0.0, 0.0, 0.0, s);
+  if (!host) return launch_stage(c, u, rhs, nullptr, false, 0.0, 0.0, 0.0, s, nullptr, t);
   if ((st = ensure_staging(c, true)) != DGW_OK) return st;
   DGW_CUDA(c, cudaMemcpyAsync(c->stage_u, u, bytes, cudaMemcpyDefault, s), "copy u in");
-  if ((st = launch_stage(c, c->stage_u, c->stage_res, nullptr, false, 0, 0, 0, s)) != DGW_OK) return st;
+  if ((st = launch_stage(c, c->stage_u, c->stage_res, nullptr, false, 0, 0, 0, s, nullptr, t)) != DGW_OK) return st;
   DGW_CUDA(c, cudaMemcpyAsync(rhs, c->stage_res, bytes, cudaMemcpyDefault, s), "copy rhs out");
   DGW_CUDA(c, cudaStreamSynchronize(s), "rhs");
   return DGW_OK;
@@ -490,7 +511,6 @@ dgw_status dgw_rhs(dgw_ctx* c, const double* u, double* rhs, double t, void* str
 
 dgw_status dgw_stage(dgw_ctx* c, const double* u_in, double* u_out, double* res, int stage, double t,
                      double dt, void* stream) {
-  (void)t;
   dgw_status st = ready(c);
   if (st != DGW_OK) return st;
   if (stage < 0 || stage > 4) return fail(c, DGW_ERR_ARG, "stage %d outside 0..4", stage);
@@ -500,12 +520,12 @@ dgw_status dgw_stage(dgw_ctx* c, const double* u_in, double* u_out, double* res,
   if (!is_device_ptr(u_in) || !is_device_ptr(u_out) || !is_device_ptr(res))
     return fail(c, DGW_ERR_ARG, "dgw_stage takes device pointers");
   if (set_device(c) != DGW_OK) return DGW_ERR_CUDA;
-  return launch_stage(c, u_in, u_out, res, true, kLsrkA[stage], kLsrkB[stage], dt, (cudaStream_t)stream);
+  return launch_stage(c, u_in, u_out, res, true, kLsrkA[stage], kLsrkB[stage], dt, (cudaStream_t)stream, nullptr,
+                      t + kLsrkC[stage] * dt);
 }
 
 dgw_status dgw_stage_energy(dgw_ctx* c, const double* u_in, double* u_out, double* res, int stage, double t,
                             double dt, double* energy_out, void* stream) {
-  (void)t;
   dgw_status st = ready(c);
   if (st != DGW_OK) return st;
   if (stage < 0 || stage > 4) return fail(c, DGW_ERR_ARG, "stage %d outside 0..4", stage);
@@ -517,7 +537,8 @@ dgw_status dgw_stage_energy(dgw_ctx* c, const double* u_in, double* u_out, doubl
     return fail(c, DGW_ERR_ARG, "dgw_stage_energy takes device pointers");
   if (set_device(c) != DGW_OK) return DGW_ERR_CUDA;
   cudaStream_t s = (cudaStream_t)stream;
-  if ((st = launch_stage(c, u_in, u_out, res, true, kLsrkA[stage], kLsrkB[stage], dt, s, c->stage_partials)) != DGW_OK)
+  if ((st = launch_stage(c, u_in, u_out, res, true, kLsrkA[stage], kLsrkB[stage], dt, s, c->stage_partials,
+                        t + kLsrkC[stage] * dt)) != DGW_OK)
     return st;
   double* result = c->stage_partials + c->stage_ctas;
   DGW_CUDA(c, dgw::launch_energy_final(c->stage_partials, c->stage_ctas, result, s), "energy reduction");
@@ -547,12 +568,14 @@ dgw_status dgw_step(dgw_ctx* c, double* u, double* res, double t0, double dt, in
     DGW_CUDA(c, cudaMemcpyAsync(ud, u, bytes, cudaMemcpyDefault, s), "copy u in");
     DGW_CUDA(c, cudaMemcpyAsync(rd, res, bytes, cudaMemcpyDefault, s), "copy res in");
   }
-  (void)t0;
   double* cur = ud;
   double* nxt = c->u2;
   for (int k = 0; k < nsteps; ++k) {
+    const double tk = t0 + k * dt;
     for (int sidx = 0; sidx < 5; ++sidx) {
-      if ((st = launch_stage(c, cur, nxt, rd, true, kLsrkA[sidx], kLsrkB[sidx], dt, s)) != DGW_OK) return st;
+      if ((st = launch_stage(c, cur, nxt, rd, true, kLsrkA[sidx], kLsrkB[sidx], dt, s, nullptr,
+                             tk + kLsrkC[sidx] * dt)) != DGW_OK)
+        return st;
       double* tmp = cur;
       cur = nxt;
       nxt = tmp;
@@ -586,6 +609,51 @@ dgw_status dgw_energy(dgw_ctx* c, const double* u, double* energy_out, void* str
   DGW_CUDA(c, cudaStreamSynchronize(s), "energy");
   *energy_out = *c->pinned;
   if (!std::isfinite(*energy_out)) return fail(c, DGW_ERR_UNSTABLE, "energy is not finite");
+  return DGW_OK;
+}
+
+dgw_status dgw_source_set(dgw_ctx* c, int64_t element, const double* xi, const double* force, double f0,
+                          double t0) {
+  if (!c) return fail(nullptr, DGW_ERR_ARG, "null context");
+  if (!c->has_mesh || !c->has_material) return fail(c, DGW_ERR_STATE, "source before mesh and material");
+  if (element < 0) {
+    dfree(c->src_w);
+    c->src_elem = -1;
+    return DGW_OK;
+  }
+  if (element >= c->nel) return fail(c, DGW_ERR_ARG, "source element %lld out of range", (long long)element);
+  if (!xi || !force) return fail(c, DGW_ERR_ARG, "null xi or force");
+  for (int a = 0; a < 3; ++a)
+    if (!(xi[a] >= -1.0 && xi[a] <= 1.0)) return fail(c, DGW_ERR_ARG, "xi must lie in [-1, 1]^3");
+  if (!(f0 > 0.0) || !std::isfinite(t0)) return fail(c, DGW_ERR_ARG, "need f0 > 0 and finite t0");
+  const int N = c->cfg.N, n = N + 1, Np = Np_of(N);
+  if (set_device(c) != DGW_OK) return DGW_ERR_CUDA;
+  std::vector<double> wj(Np), rho(1);
+  DGW_CUDA(c, cudaMemcpy(wj.data(), c->wJ + (size_t)element * Np, Np * sizeof(double), cudaMemcpyDeviceToHost),
+           "copy mass weights");
+  DGW_CUDA(c, cudaMemcpy(rho.data(), c->ec + element, sizeof(double), cudaMemcpyDeviceToHost), "copy density");
+  // Lagrange basis values at xi along each axis (product formula).
+  double l[3][dgw::kMaxN + 1];
+  for (int a = 0; a < 3; ++a)
+    for (int j = 0; j < n; ++j) {
+      double v = 1.0;
+      for (int k = 0; k < n; ++k)
+        if (k != j) v *= (xi[a] - c->ref.r[k]) / (c->ref.r[j] - c->ref.r[k]);
+      l[a][j] = v;
+    }
+  std::vector<double> w(3 * Np);
+  for (int kk = 0; kk < n; ++kk)
+    for (int jj = 0; jj < n; ++jj)
+      for (int ii = 0; ii < n; ++ii) {
+        const int node = ii + n * (jj + n * kk);
+        const double phi = l[0][ii] * l[1][jj] * l[2][kk] / (wj[node] * rho[0]);
+        for (int q = 0; q < 3; ++q) w[q * Np + node] = force[q] * phi;
+      }
+  if (!c->src_w) DGW_CUDA(c, cudaMalloc(&c->src_w, 3 * (size_t)dgw::kMaxNp() * sizeof(double)), "alloc source");
+  DGW_CUDA(c, cudaMemcpy(c->src_w, w.data(), 3 * Np * sizeof(double), cudaMemcpyHostToDevice), "copy source");
+  c->src_elem = element;
+  c->src_f0 = f0;
+  c->src_t0 = t0;
   return DGW_OK;
 }
 

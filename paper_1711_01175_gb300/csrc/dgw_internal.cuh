@@ -13,6 +13,7 @@ namespace dgw {
 
 constexpr int kMaxN = 7;
 constexpr int kFields = 9;
+constexpr int kMaxNp() { return (kMaxN + 1) * (kMaxN + 1) * (kMaxN + 1); }
 
 // Reference element on the host: GLL nodes/weights and the 1-D derivative
 // matrix D[i*(N+1)+j] = l_j'(r_i).
@@ -57,6 +58,10 @@ struct StageParams {
   double* energy_partials;  // LSRK mode, optional: one partial sum of w J u_out^T Q u_out per CTA
   const double* wJ;         // [nel][Np] (with energy_partials)
   const double* ec;         // [4][nel] energy constants (with energy_partials)
+  long long pf_elems;       // L2 prefetch distance in elements (0: off)
+  long long src_elem;       // element holding the point force, -1 for none
+  double src_amp;           // Ricker amplitude R(t + c_s dt) of this stage
+  const double* src_w;      // [3][Np]: F_q l_j(xi_s) / (rho w_j J_j)
   double D[(kMaxN + 1) * (kMaxN + 1)];
 };
 
@@ -89,6 +94,7 @@ void set_no_context_error(const std::string& msg);
 
 struct dgw_ctx {
   int device = 0;
+  int sm_count = 0;
   dgw_config cfg{};
   dgw::RefElem ref;
   long long nel = 0;
@@ -108,6 +114,9 @@ struct dgw_ctx {
   double* stage_u = nullptr;   // host-pointer staging buffers
   double* stage_res = nullptr;
   double* pinned = nullptr;    // pinned host slot for the energy value
+  double* src_w = nullptr;     // point-force weights [3][Np] (device)
+  long long src_elem = -1;
+  double src_f0 = 0.0, src_t0 = 0.0;
   std::vector<int64_t> etoe;   // host copy of the connectivity (face media)
   std::vector<int8_t> bc;
   double h_min = 0.0;

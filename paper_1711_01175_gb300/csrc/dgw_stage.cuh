@@ -114,6 +114,13 @@ __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
   const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gsrc) : "memory");
 }
+// Hint: bring [lo, hi) (rounded out to 16 B) into L2 with one bulk prefetch.
+// Callers keep the rounded range inside the buffer.
+__device__ __forceinline__ void prefetch_l2(const void* lo, const void* hi) {
+  const unsigned long long a = reinterpret_cast<unsigned long long>(lo) & ~15ull;
+  const unsigned long long b = (reinterpret_cast<unsigned long long>(hi) + 15ull) & ~15ull;
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(a), "r"((unsigned)(b - a)) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
@@ -164,6 +171,26 @@ __global__ void __launch_bounds__(Shape<N>::NT) stage_kernel(const StageParams p
   const Real* geo = static_cast<const Real*>(p.geo);
   const bool first = p.a == 0.0;
 
+  if (p.pf_elems > 0) {
+    // L2 prefetch of the tile that starts about two CTAs per SM later, so that its
+    // loads hit L2.  The tile must end before the last element: the 16-byte
+    // rounding of the range then stays inside every field of the buffers.
+    const long long ep = e0 + p.pf_elems;
+    if (t < 28 && ep + EPB < p.nel) {
+      const size_t off = static_cast<size_t>(ep) * Np;
+      const size_t len = static_cast<size_t>(EPB) * Np;
+      if (t < 9) {
+        const double* a = p.u_in + t * fstride + off;
+        prefetch_l2(a, a + len);
+      } else if (t < 19) {
+        const Real* a = geo + (t - 9) * fstride + off;
+        prefetch_l2(a, a + len);
+      } else if (LSRK && !first) {
+        const double* a = p.res + (t - 19) * fstride + off;
+        prefetch_l2(a, a + len);
+      }
+    }
+  }
   if constexpr (kPrefetch) {
     // The register res is needed only in the epilogue: start its copy now.
     if (active && !first) {
@@ -367,6 +394,11 @@ __global__ void __launch_bounds__(Shape<N>::NT) stage_kernel(const StageParams p
     rr[6] = mu * r[6];
     rr[7] = mu * r[7];
     rr[8] = mu * r[8];
+    if (e == p.src_elem) {
+      // point force (already divided by rho and the mass weight at set-up)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) rr[q] += static_cast<Real>(p.src_amp * p.src_w[q * Np + node]);
+    }
 
     if constexpr (!LSRK) {
 #pragma unroll

@@ -98,6 +98,12 @@ class Solver:
         if str(a.dtype) not in ("float64", "torch.float64"):
             raise ValueError(f"{name} must be float64")
 
+    def set_point_force(self, element: int, xi, force, f0: float, t0: float):
+        """Ricker point force in `element` at reference point xi (element -1 clears)."""
+        xi = np.ascontiguousarray(xi, dtype=np.float64)
+        force = np.ascontiguousarray(force, dtype=np.float64)
+        self._check(capi.dgw_source_set(self._ctx, int(element), _ptr(xi), _ptr(force), float(f0), float(t0)))
+
     def rhs(self, u, out, t: float = 0.0, stream=None):
         self._field_check(u, "u")
         self._field_check(out, "out")

@@ -117,6 +117,34 @@ def test_parity_workload_100_steps():
     assert rel_l2(res.cpu().numpy(), ro) < 1e-11
 
 
+def test_point_source_parity_rhs_and_step():
+    """Ricker point force: right-hand side at a given time and a full LSRK step
+    from a nonzero start time (stage times t + c_s dt)."""
+    import torch
+    c = Case(3, 4, 0.1, periodic=(True, True, False), boundary={4: wl.BC_ABSORBING, 5: wl.BC_FREE_SURFACE},
+             material=3, seed=2)
+    u0 = 1e-3 * c.u0
+    src = dict(element=13, xi=[0.3, -0.55, 0.1], force=[0.2, -1.0, 0.5], f0=6.0, t0=0.1)
+    c.solver.set_point_force(**src)
+    c.op.set_point_force(src["element"], src["xi"], src["force"], src["f0"], src["t0"])
+    ud = torch_cuda(u0)
+    out = torch.empty_like(ud)
+    c.solver.rhs(ud, out, t=0.13)
+    assert rel_l2(out.cpu().numpy(), c.op.rhs(u0, t=0.13)) < FP64_TOL
+    dt = c.solver.dt_cfl()
+    res = torch.zeros_like(ud)
+    c.solver.step(ud, res, dt, 2, t0=0.08)
+    uo, ro = u0.copy(), np.zeros_like(u0)
+    for k in range(2):
+        uo, ro = c.op.step(uo, ro, dt, t=0.08 + k * dt)
+    assert rel_l2(ud.cpu().numpy(), uo) < FP64_TOL
+    # removing the source restores the source-free operator
+    c.solver.set_point_force(-1, [0, 0, 0], [0, 0, 0], 1.0, 0.0)
+    c.op.source = None
+    c.solver.rhs(torch_cuda(u0), out, t=0.13)
+    assert rel_l2(out.cpu().numpy(), c.op.rhs(u0, t=0.13)) < FP64_TOL
+
+
 # ---------------------------------------------------------------------- energy
 def test_energy_parity_and_decay():
     import torch

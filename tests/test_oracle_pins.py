@@ -455,3 +455,40 @@ def test_free_surface_numerical_traction_vanishes():
     F = hdg_flux(An, S, um, weighted_trace(An, S, um, up))
     assert np.max(np.abs(F[..., :3])) < 1e-13
     assert np.max(np.abs(F[..., 3:])) > 1e-3
+
+
+# ------------------------------------------------------------ point source
+def test_ricker_closed_form_properties():
+    f0, t0 = 7.0, 0.2
+    t = np.linspace(t0 - 2.0, t0 + 2.0, 400001)
+    R = oracle.ricker(t, f0, t0)
+    assert abs(oracle.ricker(t0, f0, t0) - 1.0) < 1e-15
+    assert abs(np.trapezoid(R, t)) < 1e-9                       # zero mean
+    # zeros at t0 +- 1/(sqrt(2) pi f0)
+    tz = t0 + 1.0 / (np.sqrt(2.0) * np.pi * f0)
+    assert abs(oracle.ricker(tz, f0, t0)) < 1e-15
+
+
+def test_point_source_total_force_and_location():
+    """The projected source integrates to the force (partition of unity) and its
+    first moment is the source location x_s = x(xi_s) (interpolated map)."""
+    op, mesh, x = _operator(2, 4, 0.1)
+    e, xi, F = 5, np.array([0.3, -0.55, 0.1]), np.array([0.2, -1.0, 0.5])
+    op.set_point_force(e, xi, F, f0=6.0, t0=0.1)
+    t = 0.13
+    es, sn = op.source_nodal(t)
+    _, J = op.geometry(np.array([e]))
+    mass = op.w_vol * J[0]
+    R = float(oracle.ricker(t, 6.0, 0.1))
+    np.testing.assert_allclose(sn[:3] @ mass, F * R, rtol=1e-13)
+    assert np.all(sn[3:] == 0)
+    li = [oracle.lagrange_values(op.r, xi[a]) for a in range(3)]
+    l3 = np.einsum("k,j,i->kji", li[2], li[1], li[0]).ravel()
+    xs = l3 @ x[e]
+    for c in range(3):
+        np.testing.assert_allclose((sn[c] * mass) @ x[e], F[c] * R * xs, rtol=1e-12, atol=1e-15)
+    # a source at a node puts the whole force on that node
+    op.set_point_force(e, np.array([op.r[1], op.r[0], op.r[3]]), F, 6.0, 0.1)
+    _, sn2 = op.source_nodal(t)
+    node = 1 + 5 * (0 + 5 * 3)
+    assert np.count_nonzero(np.abs(sn2[0]) > 1e-14) == 1 and sn2[0, node] != 0
