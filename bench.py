@@ -334,6 +334,35 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def run_serving(args):
+    """Served latency: the same seeded request stream through continuous batching
+    and through one-at-a-time plain solves (mixed path).  Request payloads (mesh,
+    medium, point force) are prepared before the clock starts, as a client would
+    send them."""
+    from paper_1711_01175_gb300 import serving, reference_nodes
+    reqs = wl.make_requests(args.serve_requests, seed=7, rate=args.serve_rate,
+                            E_range=(8, args.serve_max_E), N_choices=(3, 4, 5),
+                            steps_range=(args.serve_min_steps, args.serve_max_steps))
+    for r in reqs:
+        r.payload = r.build(reference_nodes(r.N)[0])
+    warm = wl.make_requests(3, seed=8, rate=1000.0, E_range=(2, 3), N_choices=(3, 4, 5), steps_range=(2, 4))
+    for r in warm:
+        r.payload = r.build(reference_nodes(r.N)[0])
+    serving.continuous_batching(warm, precision="mixed")
+    serving.one_at_a_time(warm, precision="mixed")
+    res_b, wall_b = serving.continuous_batching(reqs, precision="mixed", memory_budget=args.serve_memory_gb * 1e9)
+    res_s, wall_s = serving.one_at_a_time(reqs, precision="mixed")
+    dof_stages = sum(r.E ** 3 * (r.N + 1) ** 3 * 9 * 5 * r.steps for r in reqs)
+    b, s1 = serving.summarize(res_b, wall_b), serving.summarize(res_s, wall_s)
+    b["dof_stage_updates_per_s"] = dof_stages / wall_b
+    s1["dof_stage_updates_per_s"] = dof_stages / wall_s
+    return {"requests": len(reqs), "rate_per_s": args.serve_rate, "mesh_E": [8, args.serve_max_E], "N": [3, 4, 5],
+            "steps": [args.serve_min_steps, args.serve_max_steps], "precision": "mixed",
+            "memory_budget_gb": args.serve_memory_gb,
+            "continuous_batching": b, "one_at_a_time": s1,
+            "p99_ms": b["p99_ms"], "p50_ms": b["p50_ms"]}
+
+
 def build_workload_oracle(name, E=None):
     import oracle
     cfg = workload_config(name, E)
@@ -355,6 +384,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=256, help="elements per reference-arm step")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=48,
+                    help="requests of the served-latency run (the full recipe: 2000)")
+    ap.add_argument("--serve-rate", type=float, default=80.0, help="Poisson arrival rate per second")
+    ap.add_argument("--serve-max-E", type=int, default=20, help="largest mesh edge (the full recipe: 48)")
+    ap.add_argument("--serve-min-steps", type=int, default=40, help="(the full recipe: 200)")
+    ap.add_argument("--serve-max-steps", type=int, default=120, help="(the full recipe: 2000)")
+    ap.add_argument("--serve-memory-gb", type=float, default=40.0, help="device memory the server may hold")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -447,6 +484,8 @@ def main():
         line["e2e"] = head["e2e"]
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_sample(cfg, data)
+    if world == 1 and not args.no_serving:
+        line["serving"] = run_serving(args)
     if len(results) > 1:
         m = results["mixed"]
         line["variants"] = {"mixed": {"value": m["value"], "dtype": "f32/f64", "steps": m["steps"],

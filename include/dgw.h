@@ -64,7 +64,7 @@ typedef struct {
 } dgw_config;
 
 /* ABI version of this header (bumped on any signature change). */
-#define DGW_ABI_VERSION 3
+#define DGW_ABI_VERSION 4
 int dgw_abi_version(void);
 
 /* GLL nodes r[0..N] (ascending, r[0] = -1, r[N] = +1) and weights w[0..N]
@@ -169,6 +169,39 @@ dgw_status dgw_adjoint_step(dgw_ctx* ctx, double* lam_u, double* lam_res, double
  * P-wave speed sqrt((lam + 2 mu) / rho); the CFL convention of the paper's
  * time-dependent transport experiments (Section 6.1). */
 dgw_status dgw_dt_cfl(dgw_ctx* ctx, double* dt_out);
+
+/* ---- Batches: many solves advanced together (serving) -------------------
+ * A batch advances solves of one degree N, precision and flux choice, each
+ * owned by its own context (mesh, medium, point force), in lock step: every
+ * launch of the persistent batched stage kernel covers the elements of all
+ * of them.  Not part of the paper (its runs are single solves); the
+ * arithmetic per element is the one of dgw_stage. */
+typedef struct dgw_batch dgw_batch;
+
+/* Create an empty batch for degree N, precision and flux_tau on `device`. */
+dgw_status dgw_batch_create(dgw_batch** out, int device, int N, int precision, int flux_tau);
+
+/* Free the batch (not the contexts or buffers it referenced; NULL accepted). */
+dgw_status dgw_batch_destroy(dgw_batch* b);
+
+/* Make the batch advance n solves: ctxs[i] (same N, precision, flux, device;
+ * mesh and material uploaded), u[i] and res[i] (distinct device buffers
+ * [9][nel_i][Np], the state in and out and the LSRK register), step size
+ * dt[i] and current time t0[i] (for the point force).  The context's second
+ * state buffer serves as the stage ping-pong partner, so a context belongs to
+ * at most one batch at a time.  Uploads the descriptors on `stream` (and
+ * waits for it), then records a CUDA graph of two LSRK steps on a private
+ * stream of the batch.  Call again whenever the set of solves changes,
+ * passing each continuing solve's current time. */
+dgw_status dgw_batch_set(dgw_batch* b, int n, dgw_ctx* const* ctxs, double* const* u, double* const* res,
+                         const double* dt, const double* t0, void* stream);
+
+/* Advance every solve of the batch by 2 * npairs LSRK steps (graph replays
+ * enqueued on `stream`; asynchronous). */
+dgw_status dgw_batch_run(dgw_batch* b, int npairs, void* stream);
+
+/* Message of the last failing batch call (b may be NULL). */
+const char* dgw_batch_last_error(const dgw_batch* b);
 
 /* Discrete energy for callers that cannot allocate device memory.
  * The paper has no counterpart: this is a deployment convenience.  Some

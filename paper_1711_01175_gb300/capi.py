@@ -46,6 +46,11 @@ SIGNATURES = {
     "dgw_source_set": (_I, [_P, _I64, _P, _P, _D, _D]),
     "dgw_adjoint_step": (_I, [_P, _P, _P, _P, _P, _D, _D, _I, _P]),
     "dgw_dt_cfl": (_I, [_P, ctypes.POINTER(_D)]),
+    "dgw_batch_create": (_I, [ctypes.POINTER(_P), _I, _I, _I, _I]),
+    "dgw_batch_destroy": (_I, [_P]),
+    "dgw_batch_set": (_I, [_P, _I, _P, _P, _P, _P, _P, _P]),
+    "dgw_batch_run": (_I, [_P, _I, _P]),
+    "dgw_batch_last_error": (ctypes.c_char_p, [_P]),
     "dgw_energy_static": (_I, [_I, _I64, _P, _P, _P, _P, _P, _P, _P]),
     "dgw_last_error": (ctypes.c_char_p, [_P]),
 }
@@ -146,6 +151,28 @@ def dgw_dt_cfl(ctx):
     out = _D()
     st = load().dgw_dt_cfl(ctx, ctypes.byref(out))
     return st, out.value
+
+
+def dgw_batch_create(device, N, precision, flux_tau):
+    h = _P()
+    st = load().dgw_batch_create(ctypes.byref(h), device, N, precision, flux_tau)
+    return st, h
+
+
+def dgw_batch_destroy(b):
+    return load().dgw_batch_destroy(b)
+
+
+def dgw_batch_set(b, n, ctxs, u, res, dt, t0, stream):
+    return load().dgw_batch_set(b, n, ctxs, u, res, dt, t0, stream)
+
+
+def dgw_batch_run(b, npairs, stream):
+    return load().dgw_batch_run(b, npairs, stream)
+
+
+def dgw_batch_last_error(b):
+    return load().dgw_batch_last_error(b).decode(errors="replace")
 
 
 def dgw_energy_static(N, nel, x, u, rho, lam, mu, energy_out, stream):

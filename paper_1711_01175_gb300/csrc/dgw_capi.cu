@@ -249,7 +249,12 @@ dgw_status dgw_create(dgw_ctx** out, int device, const dgw_config* cfg) {
     return fail(nullptr, DGW_ERR_CUDA, "cudaSetDevice(%d) failed", device);
   }
   cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+  if (cudaStreamCreateWithFlags(&c->setup, cudaStreamNonBlocking) != cudaSuccess) {
+    delete c;
+    return fail(nullptr, DGW_ERR_CUDA, "set-up stream");
+  }
   if (cudaMallocHost((void**)&c->pinned, sizeof(double)) != cudaSuccess) {
+    cudaStreamDestroy(c->setup);
     delete c;
     return fail(nullptr, DGW_ERR_OOM, "pinned host slot");
   }
@@ -262,6 +267,7 @@ dgw_status dgw_destroy(dgw_ctx* c) {
   cudaSetDevice(c->device);
   free_mesh(c);
   if (c->pinned) cudaFreeHost(c->pinned);
+  if (c->setup) cudaStreamDestroy(c->setup);
   delete c;
   return DGW_OK;
 }
@@ -386,15 +392,16 @@ dgw_status dgw_mesh_upload(dgw_ctx* c, int64_t nel, const double* x, const int64
     c->stage_ctas = (int)((nel + epb - 1) / epb);
     DGW_TRY(cudaMalloc(&c->stage_partials, ((size_t)c->stage_ctas + 1) * sizeof(double)), "alloc stage energy partials");
   }
-  DGW_TRY(cudaMemcpy(x_d, x, nodes * 3 * sizeof(double), cudaMemcpyHostToDevice), "copy x");
-  DGW_TRY(cudaMemcpy(D_d, c->ref.D, sizeof(c->ref.D), cudaMemcpyHostToDevice), "copy D");
-  DGW_TRY(cudaMemcpy(w_d, c->ref.w, sizeof(c->ref.w), cudaMemcpyHostToDevice), "copy w");
-  DGW_TRY(cudaMemcpy(c->vmapP, vmap.data(), fnodes * sizeof(int), cudaMemcpyHostToDevice), "copy neighbour map");
+  DGW_TRY(cudaMemcpyAsync(x_d, x, nodes * 3 * sizeof(double), cudaMemcpyHostToDevice, c->setup), "copy x");
+  DGW_TRY(cudaMemcpyAsync(D_d, c->ref.D, sizeof(c->ref.D), cudaMemcpyHostToDevice, c->setup), "copy D");
+  DGW_TRY(cudaMemcpyAsync(w_d, c->ref.w, sizeof(c->ref.w), cudaMemcpyHostToDevice, c->setup), "copy w");
+  DGW_TRY(cudaMemcpyAsync(c->vmapP, vmap.data(), fnodes * sizeof(int), cudaMemcpyHostToDevice, c->setup), "copy neighbour map");
   dgw::GeometryOut go{geo64, c->wJ, minJ};
-  DGW_TRY(dgw::launch_geometry(N, x_d, nel, D_d, w_d, go, 0), "geometry kernel");
-  DGW_TRY(cudaDeviceSynchronize(), "geometry kernel");
+  DGW_TRY(dgw::launch_geometry(N, x_d, nel, D_d, w_d, go, c->setup), "geometry kernel");
+  DGW_TRY(cudaStreamSynchronize(c->setup), "geometry kernel");
   std::vector<double> mj(nel);
-  DGW_TRY(cudaMemcpy(mj.data(), minJ, nel * sizeof(double), cudaMemcpyDeviceToHost), "copy minJ");
+  DGW_TRY(cudaMemcpyAsync(mj.data(), minJ, nel * sizeof(double), cudaMemcpyDeviceToHost, c->setup), "copy minJ");
+  DGW_TRY(cudaStreamSynchronize(c->setup), "copy minJ");
   for (int64_t e = 0; e < nel; ++e) {
     if (!(mj[e] > 0.0)) {
       cleanup();
@@ -406,8 +413,8 @@ dgw_status dgw_mesh_upload(dgw_ctx* c, int64_t nel, const double* x, const int64
     float* g32 = nullptr;
     DGW_TRY(cudaMalloc(&g32, nodes * 10 * sizeof(float)), "alloc geometry fp32");
     c->geo = g32;
-    DGW_TRY(dgw::launch_to_float(geo64, g32, nodes * 10, 0), "geometry to fp32");
-    DGW_TRY(cudaDeviceSynchronize(), "geometry to fp32");
+    DGW_TRY(dgw::launch_to_float(geo64, g32, nodes * 10, c->setup), "geometry to fp32");
+    DGW_TRY(cudaStreamSynchronize(c->setup), "geometry to fp32");
   } else {
     c->geo = geo64;
   }
@@ -466,20 +473,21 @@ dgw_status dgw_material_upload(dgw_ctx* c, const double* rho, const double* lam,
   c->src_elem = -1;
   c->has_material = false;
   DGW_CUDA(c, cudaMalloc(&c->ec, 4 * nel * sizeof(double)), "alloc energy constants");
-  DGW_CUDA(c, cudaMemcpy(c->ec, ec.data(), 4 * nel * sizeof(double), cudaMemcpyHostToDevice), "copy energy constants");
+  DGW_CUDA(c, cudaMemcpyAsync(c->ec, ec.data(), 4 * nel * sizeof(double), cudaMemcpyHostToDevice, c->setup), "copy energy constants");
   if (c->cfg.precision == DGW_PRECISION_MIXED) {
     std::vector<float> m32(m64.begin(), m64.end());
     std::vector<float> fz32(fz.begin(), fz.end());
     DGW_CUDA(c, cudaMalloc(&c->mat, 3 * nel * sizeof(float)), "alloc material");
-    DGW_CUDA(c, cudaMemcpy(c->mat, m32.data(), 3 * nel * sizeof(float), cudaMemcpyHostToDevice), "copy material");
+    DGW_CUDA(c, cudaMemcpyAsync(c->mat, m32.data(), 3 * nel * sizeof(float), cudaMemcpyHostToDevice, c->setup), "copy material");
     DGW_CUDA(c, cudaMalloc(&c->fz, fz32.size() * sizeof(float)), "alloc face media");
-    DGW_CUDA(c, cudaMemcpy(c->fz, fz32.data(), fz32.size() * sizeof(float), cudaMemcpyHostToDevice), "copy face media");
+    DGW_CUDA(c, cudaMemcpyAsync(c->fz, fz32.data(), fz32.size() * sizeof(float), cudaMemcpyHostToDevice, c->setup), "copy face media");
   } else {
     DGW_CUDA(c, cudaMalloc(&c->mat, 3 * nel * sizeof(double)), "alloc material");
-    DGW_CUDA(c, cudaMemcpy(c->mat, m64.data(), 3 * nel * sizeof(double), cudaMemcpyHostToDevice), "copy material");
+    DGW_CUDA(c, cudaMemcpyAsync(c->mat, m64.data(), 3 * nel * sizeof(double), cudaMemcpyHostToDevice, c->setup), "copy material");
     DGW_CUDA(c, cudaMalloc(&c->fz, fz.size() * sizeof(double)), "alloc face media");
-    DGW_CUDA(c, cudaMemcpy(c->fz, fz.data(), fz.size() * sizeof(double), cudaMemcpyHostToDevice), "copy face media");
+    DGW_CUDA(c, cudaMemcpyAsync(c->fz, fz.data(), fz.size() * sizeof(double), cudaMemcpyHostToDevice, c->setup), "copy face media");
   }
+  DGW_CUDA(c, cudaStreamSynchronize(c->setup), "material upload");
   c->c_max = cmax;
   c->has_material = true;
   return DGW_OK;
@@ -629,9 +637,11 @@ dgw_status dgw_source_set(dgw_ctx* c, int64_t element, const double* xi, const d
   const int N = c->cfg.N, n = N + 1, Np = Np_of(N);
   if (set_device(c) != DGW_OK) return DGW_ERR_CUDA;
   std::vector<double> wj(Np), rho(1);
-  DGW_CUDA(c, cudaMemcpy(wj.data(), c->wJ + (size_t)element * Np, Np * sizeof(double), cudaMemcpyDeviceToHost),
-           "copy mass weights");
-  DGW_CUDA(c, cudaMemcpy(rho.data(), c->ec + element, sizeof(double), cudaMemcpyDeviceToHost), "copy density");
+  DGW_CUDA(c, cudaMemcpyAsync(wj.data(), c->wJ + (size_t)element * Np, Np * sizeof(double), cudaMemcpyDeviceToHost,
+                              c->setup), "copy mass weights");
+  DGW_CUDA(c, cudaMemcpyAsync(rho.data(), c->ec + element, sizeof(double), cudaMemcpyDeviceToHost, c->setup),
+           "copy density");
+  DGW_CUDA(c, cudaStreamSynchronize(c->setup), "copy source data");
   // Lagrange basis values at xi along each axis (product formula).
   double l[3][dgw::kMaxN + 1];
   for (int a = 0; a < 3; ++a)
@@ -650,7 +660,9 @@ dgw_status dgw_source_set(dgw_ctx* c, int64_t element, const double* xi, const d
         for (int q = 0; q < 3; ++q) w[q * Np + node] = force[q] * phi;
       }
   if (!c->src_w) DGW_CUDA(c, cudaMalloc(&c->src_w, 3 * (size_t)dgw::kMaxNp() * sizeof(double)), "alloc source");
-  DGW_CUDA(c, cudaMemcpy(c->src_w, w.data(), 3 * Np * sizeof(double), cudaMemcpyHostToDevice), "copy source");
+  DGW_CUDA(c, cudaMemcpyAsync(c->src_w, w.data(), 3 * Np * sizeof(double), cudaMemcpyHostToDevice, c->setup),
+           "copy source");
+  DGW_CUDA(c, cudaStreamSynchronize(c->setup), "copy source");
   c->src_elem = element;
   c->src_f0 = f0;
   c->src_t0 = t0;

@@ -65,7 +65,40 @@ struct StageParams {
   double D[(kMaxN + 1) * (kMaxN + 1)];
 };
 
+// One solve of a batch (device descriptor).
+struct BatchSolve {
+  double* u[2];           // state ping-pong: u[0] is the caller's state, u[1] the context's second buffer
+  double* res;            // LSRK register
+  const void* geo;
+  const void* fz;
+  const int* vmapP;
+  const void* mat;
+  long long nel;
+  double dt;
+  long long src_elem;
+  const double* src_w;
+  double src_f0, src_t0;
+  double* t;              // device start time of the current step pair
+  long long tile0;        // first batch tile of this solve
+};
+
+// One launch of the batched stage kernel.
+struct BatchLaunch {
+  const BatchSolve* solves;
+  int nsolves;
+  long long total_tiles;
+  int parity;             // stage index within the replayed step pair, mod 2
+  int step;               // step within the pair (0 or 1)
+  double a, b, c;         // LSRK coefficients of this stage
+  double tau;
+  double w_end_inv;
+  long long pf_elems;
+  double D[(kMaxN + 1) * (kMaxN + 1)];
+};
+
 // Launchers implemented in dgw_stage_fp64.cu / dgw_stage_mixed.cu.
+cudaError_t launch_stage_batch(int N, bool mixed, const BatchLaunch& L, int grid, cudaStream_t s);
+cudaError_t prepare_stage_batch(int N, bool mixed, int sm_count, int* grid);
 cudaError_t launch_stage_fp64(int N, bool lsrk, const StageParams& p, cudaStream_t s);
 cudaError_t launch_stage_mixed(int N, bool lsrk, const StageParams& p, cudaStream_t s);
 void stage_shape(int N, int* epb, int* threads);
@@ -95,6 +128,7 @@ void set_no_context_error(const std::string& msg);
 struct dgw_ctx {
   int device = 0;
   int sm_count = 0;
+  cudaStream_t setup = nullptr;    // private non-blocking stream for uploads and geometry
   dgw_config cfg{};
   dgw::RefElem ref;
   long long nel = 0;

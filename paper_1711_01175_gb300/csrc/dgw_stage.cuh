@@ -139,8 +139,10 @@ struct StageSmem {
   static constexpr size_t bytes = r_off + (kPrefetchRes ? sizeof(double) * 9 * S::NTILE : 0);
 };
 
+// One tile (EPB consecutive elements) of one solve.  The caller has filled the
+// D tile of shared memory; p may live in parameter or shared memory.
 template <int N, typename Real, bool LSRK>
-__global__ void __launch_bounds__(Shape<N>::NT) stage_kernel(const StageParams p) {
+__device__ __forceinline__ void stage_tile(const StageParams& p, long long tile, unsigned char* smem_raw) {
   using S = Shape<N>;
   using L = StageSmem<N, Real>;
   using V = Pack<Real>;
@@ -148,7 +150,6 @@ __global__ void __launch_bounds__(Shape<N>::NT) stage_kernel(const StageParams p
   constexpr int NTILE = S::NTILE, NFI = S::NFACE_ITEMS, PK = L::PK;
   constexpr bool kPrefetch = LSRK && L::kPrefetchRes;
 
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* u_s = reinterpret_cast<Real*>(smem_raw + L::u_off);
   Real* f_s = reinterpret_cast<Real*>(smem_raw + L::f_off);
   Real* x_s = f_s;                       // face fluxes [9][NFI] reuse the flux tile
@@ -158,9 +159,7 @@ __global__ void __launch_bounds__(Shape<N>::NT) stage_kernel(const StageParams p
   double* red_s = reinterpret_cast<double*>(smem_raw + L::e_off);
 
   const int t = threadIdx.x;
-  for (int i = t; i < n * n; i += NT) D_s[i] = static_cast<Real>(p.D[i]);
-
-  const long long e0 = static_cast<long long>(blockIdx.x) * EPB;
+  const long long e0 = tile * EPB;
   const int el = t / Np;
   const int node = t - el * Np;
   const long long e = e0 + el;
@@ -457,9 +456,120 @@ __global__ void __launch_bounds__(Shape<N>::NT) stage_kernel(const StageParams p
       if (t < 32) {
         double w2 = t < NT / 32 ? red_s[t] : 0.0;
         for (int off = 16; off > 0; off >>= 1) w2 += __shfl_down_sync(0xffffffffu, w2, off);
-        if (t == 0) p.energy_partials[blockIdx.x] = w2;
+        if (t == 0) p.energy_partials[tile] = w2;
       }
     }
+  }
+}
+
+template <int N, typename Real, bool LSRK>
+__global__ void __launch_bounds__(Shape<N>::NT) stage_kernel(const StageParams p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* D_s = reinterpret_cast<Real*>(smem_raw + StageSmem<N, Real>::d_off);
+  for (int i = threadIdx.x; i < Shape<N>::n * Shape<N>::n; i += Shape<N>::NT) D_s[i] = static_cast<Real>(p.D[i]);
+  stage_tile<N, Real, LSRK>(p, blockIdx.x, smem_raw);
+}
+
+__device__ __forceinline__ double ricker_dev(double t, double f0, double t0) {
+  const double a = 3.14159265358979323846 * f0 * (t - t0);
+  return (1.0 - 2.0 * a * a) * exp(-a * a);
+}
+
+// Persistent batched stage: CTAs walk the tiles of every solve of the batch
+// (solves of one degree and precision, each with its own mesh, medium, state
+// and source).  Thread 0 builds the solve's stage parameters in shared memory;
+// the stage time of the source is t + (step + c_s) dt with t read from device
+// memory, so the launches can be replayed from a CUDA graph.
+template <int N, typename Real>
+__global__ void __launch_bounds__(Shape<N>::NT) stage_batch_kernel(const BatchLaunch L) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ StageParams ps;
+  __shared__ long long local_tile;
+  Real* D_s = reinterpret_cast<Real*>(smem_raw + StageSmem<N, Real>::d_off);
+  for (int i = threadIdx.x; i < Shape<N>::n * Shape<N>::n; i += Shape<N>::NT) D_s[i] = static_cast<Real>(L.D[i]);
+  for (long long tile = blockIdx.x; tile < L.total_tiles; tile += gridDim.x) {
+    if (threadIdx.x == 0) {
+      int lo = 0, hi = L.nsolves - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (L.solves[mid].tile0 <= tile) lo = mid; else hi = mid - 1;
+      }
+      const BatchSolve& b = L.solves[lo];
+      ps.u_in = b.u[L.parity];
+      ps.out = b.u[L.parity ^ 1];
+      ps.res = b.res;
+      ps.geo = b.geo;
+      ps.fz = b.fz;
+      ps.vmapP = b.vmapP;
+      ps.mat = b.mat;
+      ps.nel = b.nel;
+      ps.a = L.a;
+      ps.b = L.b;
+      ps.dt = b.dt;
+      ps.tau = L.tau;
+      ps.w_end_inv = L.w_end_inv;
+      ps.energy_partials = nullptr;
+      ps.wJ = nullptr;
+      ps.ec = nullptr;
+      ps.pf_elems = L.pf_elems;
+      ps.src_elem = b.src_elem;
+      ps.src_w = b.src_w;
+      ps.src_amp = b.src_elem >= 0 ? ricker_dev(*b.t + (L.step + L.c) * b.dt, b.src_f0, b.src_t0) : 0.0;
+      local_tile = tile - b.tile0;
+    }
+    __syncthreads();
+    stage_tile<N, Real, true>(ps, local_tile, smem_raw);
+    __syncthreads();
+  }
+}
+
+template <int N, typename Real>
+cudaError_t launch_stage_batch_t(const BatchLaunch& L, int grid, cudaStream_t s) {
+  const size_t smem = StageSmem<N, Real>::bytes;
+  stage_batch_kernel<N, Real><<<grid, Shape<N>::NT, smem, s>>>(L);
+  return cudaGetLastError();
+}
+
+// Set the kernel attributes and return the persistent grid (resident CTAs).
+template <int N, typename Real>
+cudaError_t prepare_stage_batch_t(int sm_count, int* grid) {
+  const size_t smem = StageSmem<N, Real>::bytes;
+  cudaError_t err = cudaFuncSetAttribute(stage_batch_kernel<N, Real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+  if (err != cudaSuccess) return err;
+  err = cudaFuncSetAttribute(stage_batch_kernel<N, Real>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+  if (err != cudaSuccess) return err;
+  int per_sm = 0;
+  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_batch_kernel<N, Real>, Shape<N>::NT, smem);
+  if (err != cudaSuccess) return err;
+  *grid = (per_sm > 0 ? per_sm : 1) * sm_count;
+  return cudaSuccess;
+}
+
+template <typename Real>
+cudaError_t launch_stage_batch_any(int N, const BatchLaunch& L, int grid, cudaStream_t s) {
+  switch (N) {
+#define DGW_BCASE(NN) \
+  case NN:            \
+    return launch_stage_batch_t<NN, Real>(L, grid, s);
+    DGW_BCASE(1) DGW_BCASE(2) DGW_BCASE(3) DGW_BCASE(4) DGW_BCASE(5) DGW_BCASE(6) DGW_BCASE(7)
+#undef DGW_BCASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+template <typename Real>
+cudaError_t prepare_stage_batch_any(int N, int sm_count, int* grid) {
+  switch (N) {
+#define DGW_PCASE(NN) \
+  case NN:            \
+    return prepare_stage_batch_t<NN, Real>(sm_count, grid);
+    DGW_PCASE(1) DGW_PCASE(2) DGW_PCASE(3) DGW_PCASE(4) DGW_PCASE(5) DGW_PCASE(6) DGW_PCASE(7)
+#undef DGW_PCASE
+    default:
+      return cudaErrorInvalidValue;
   }
 }
 

@@ -22,4 +22,12 @@ void stage_shape(int N, int* epb, int* threads) {
   }
 }
 
+cudaError_t launch_stage_batch_fp64(int N, const BatchLaunch& L, int grid, cudaStream_t s) {
+  return launch_stage_batch_any<double>(N, L, grid, s);
+}
+
+cudaError_t prepare_stage_batch_fp64(int N, int sm_count, int* grid) {
+  return prepare_stage_batch_any<double>(N, sm_count, grid);
+}
+
 }  // namespace dgw

@@ -1,0 +1,186 @@
+"""Serving loop: continuous batching of independent wave solves on one GPU.
+
+Requests arrive over time (each its own mesh, degree, medium, point force and
+step count).  The server admits a waiting request as soon as its device
+memory fits the budget, keeps every admitted solve's fields on the device,
+and advances all admitted solves of one degree together through a
+`dgw_batch` (one persistent batched stage kernel per stage over the elements
+of every solve, replayed from a captured CUDA graph of two LSRK steps).
+Solves of different degrees run in separate batches on separate streams, so
+their work overlaps on the device.  Between graph replays the server admits
+new arrivals and retires finished solves (their composition change makes the
+batch capture a new graph).  Latency is arrival -> result on the host.
+
+`one_at_a_time` is the reference policy: requests are served strictly in
+arrival order, each alone with dgw_step.
+"""
+from __future__ import annotations
+
+import ctypes
+import time
+from collections import deque
+
+import numpy as np
+
+from . import capi
+from .solver import Solver, reference_nodes
+
+
+def bytes_per_request(E, N, precision):
+    """Device memory a solve holds: three FP64 state-sized buffers (u, the
+    context's second buffer, res), the metric terms in the path's precision,
+    mass weights and the neighbour map."""
+    nel = E ** 3
+    Np = (N + 1) ** 3
+    real = 4 if precision == "mixed" else 8
+    per_node = 3 * 9 * 8 + 10 * real + 8 + 6 * (N + 1) ** 2 * 4 / Np
+    return int(nel * Np * per_node + nel * 200)
+
+
+class _Solve:
+    def __init__(self, req, precision, stream):
+        import torch
+        r, _ = reference_nodes(req.N)
+        d = req.payload if req.payload else req.build(r)
+        m = d["mesh"]
+        self.req = req
+        self.solver = Solver(req.N, tau=1, precision=precision)
+        self.solver.upload_mesh(d["x"], m.etoe, m.etof, m.orient, m.bc)
+        self.solver.upload_material(d["rho"], d["lam"], d["mu"])
+        self.solver.set_point_force(**d["source"])
+        self.dt = self.solver.dt_cfl()
+        with torch.cuda.stream(stream):
+            self.u = torch.zeros((9, m.nel, (req.N + 1) ** 3), dtype=torch.float64, device="cuda")
+            self.res = torch.zeros_like(self.u)
+        self.steps_done = 0
+        self.bytes = bytes_per_request(req.E, req.N, precision)
+
+    def close(self):
+        self.solver.close()
+        self.u = self.res = None
+
+
+class _Group:
+    """The batch of one degree and its stream."""
+
+    def __init__(self, N, precision):
+        import torch
+        self.N = N
+        self.stream = torch.cuda.Stream()
+        st, self.h = capi.dgw_batch_create(torch.cuda.current_device(), N, 0 if precision == "fp64" else 1, 1)
+        if st != 0:
+            raise capi.DGWError(st, capi.dgw_last_error(None))
+        self.solves = []
+        self.dirty = False
+        self.event = None
+
+    def reset(self):
+        n = len(self.solves)
+        P = ctypes.c_void_p * max(n, 1)
+        D = ctypes.c_double * max(n, 1)
+        st = capi.dgw_batch_set(self.h, n, P(*[s.solver._ctx.value for s in self.solves]),
+                                P(*[s.u.data_ptr() for s in self.solves]),
+                                P(*[s.res.data_ptr() for s in self.solves]),
+                                D(*[s.dt for s in self.solves]),
+                                D(*[s.steps_done * s.dt for s in self.solves]),
+                                ctypes.c_void_p(self.stream.cuda_stream))
+        if st != 0:
+            raise capi.DGWError(st, capi.dgw_batch_last_error(self.h))
+        self.dirty = False
+
+    def close(self):
+        capi.dgw_batch_destroy(self.h)
+
+
+def _finish(solve, t0):
+    """Result on the host: the final state's energy and the state itself."""
+    u = solve.u.cpu().numpy()
+    e = solve.solver.energy(solve.u)
+    return dict(rid=solve.req.rid, energy=e, state=u, done=time.perf_counter() - t0)
+
+
+def continuous_batching(requests, precision="mixed", memory_budget=40e9, pairs_per_tick=4, keep_states=False):
+    """Serve `requests` (sorted by arrival) with continuous batching."""
+    import torch
+    pending = deque(sorted(requests, key=lambda r: r.arrival))
+    waiting = deque()
+    groups = {}
+    used = 0
+    results = {}
+    t0 = time.perf_counter()
+    while pending or waiting or any(g.solves for g in groups.values()):
+        now = time.perf_counter() - t0
+        while pending and pending[0].arrival <= now:
+            waiting.append(pending.popleft())
+        while waiting and used + bytes_per_request(waiting[0].E, waiting[0].N, precision) <= memory_budget:
+            req = waiting.popleft()
+            g = groups.get(req.N)
+            if g is None:
+                g = groups[req.N] = _Group(req.N, precision)
+            s = _Solve(req, precision, g.stream)
+            used += s.bytes
+            g.solves.append(s)
+            g.dirty = True
+        active = [g for g in groups.values() if g.solves]
+        if not active:
+            if pending:
+                time.sleep(max(0.0, pending[0].arrival - (time.perf_counter() - t0)))
+            continue
+        for g in active:
+            if g.dirty:
+                g.reset()
+            k = min(pairs_per_tick, min((s.req.steps - s.steps_done) // 2 for s in g.solves))
+            st = capi.dgw_batch_run(g.h, k, ctypes.c_void_p(g.stream.cuda_stream))
+            if st != 0:
+                raise capi.DGWError(st, capi.dgw_batch_last_error(g.h))
+            for s in g.solves:
+                s.steps_done += 2 * k
+            g.event = torch.cuda.Event()
+            g.event.record(g.stream)
+        for g in active:
+            g.event.synchronize()
+            finished = [s for s in g.solves if s.steps_done >= s.req.steps]
+            if finished:
+                g.solves = [s for s in g.solves if s.steps_done < s.req.steps]
+                g.dirty = True
+                for s in finished:
+                    r = _finish(s, t0)
+                    r["latency"] = r["done"] - s.req.arrival
+                    if not keep_states:
+                        r.pop("state")
+                    results[s.req.rid] = r
+                    used -= s.bytes
+                    s.close()
+    for g in groups.values():
+        g.close()
+    return results, time.perf_counter() - t0
+
+
+def one_at_a_time(requests, precision="mixed", keep_states=False):
+    """Serve `requests` strictly in arrival order, one solve at a time (dgw_step)."""
+    import torch
+    stream = torch.cuda.Stream()
+    results = {}
+    t0 = time.perf_counter()
+    for req in sorted(requests, key=lambda r: r.arrival):
+        wait = req.arrival - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        s = _Solve(req, precision, stream)
+        with torch.cuda.stream(stream):
+            s.solver.step(s.u, s.res, s.dt, req.steps, t0=0.0, stream=stream)
+        stream.synchronize()
+        s.steps_done = req.steps
+        r = _finish(s, t0)
+        r["latency"] = r["done"] - req.arrival
+        if not keep_states:
+            r.pop("state")
+        results[req.rid] = r
+        s.close()
+    return results, time.perf_counter() - t0
+
+
+def summarize(results, wall):
+    lat = np.array([r["latency"] for r in results.values()]) * 1e3
+    return {"requests": len(results), "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "solves_per_s": len(results) / wall, "wall_s": wall}

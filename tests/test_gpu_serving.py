@@ -1,0 +1,57 @@
+"""Serving loop: continuous batching gives each request the result it gets alone.
+
+Requests with different meshes, degrees, media, point forces and step counts
+arrive while others run; the batched server admits them as memory frees up.
+Each final state must equal the one from serving the requests one at a time
+(dgw_step), within the path's tolerance: 1e-12 relative L2 for FP64 (the
+batch computes the source amplitude from a device-side time, so agreement is
+to rounding), 1e-6 for the mixed path (an FP32 rounding of the point force
+can flip where the amplitude differs in its last bit).
+"""
+import numpy as np
+import pytest
+
+import workloads as wl
+from harness import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__ as g
+    g.build()
+
+
+def _requests():
+    reqs = wl.make_requests(8, seed=3, rate=40.0, E_range=(2, 5), N_choices=(3, 4), steps_range=(4, 16))
+    from paper_1711_01175_gb300 import reference_nodes
+    for r in reqs:
+        r.payload = r.build(reference_nodes(r.N)[0])
+    return reqs
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-6)])
+def test_each_result_same_alone_and_in_the_mix(precision, tol):
+    from paper_1711_01175_gb300 import serving
+    reqs = _requests()
+    mixed, wall = serving.continuous_batching(reqs, precision=precision, keep_states=True, pairs_per_tick=2)
+    alone, _ = serving.one_at_a_time(reqs, precision=precision, keep_states=True)
+    assert sorted(mixed) == sorted(alone) == [r.rid for r in reqs]
+    for rid in mixed:
+        a, b = mixed[rid]["state"], alone[rid]["state"]
+        assert np.linalg.norm(b) > 0
+        assert rel_l2(a, b) < tol, (rid, rel_l2(a, b))
+        assert abs(mixed[rid]["energy"] - alone[rid]["energy"]) <= 1e3 * tol * alone[rid]["energy"]
+    s = serving.summarize(mixed, wall)
+    assert s["p99_ms"] >= s["p50_ms"] > 0
+
+
+def test_memory_budget_admits_as_memory_frees():
+    from paper_1711_01175_gb300 import serving
+    reqs = _requests()
+    biggest = max(serving.bytes_per_request(r.E, r.N, "fp64") for r in reqs)
+    res, _ = serving.continuous_batching(reqs, precision="fp64", memory_budget=biggest * 1.5, keep_states=True)
+    alone, _ = serving.one_at_a_time(reqs, precision="fp64", keep_states=True)
+    for rid in res:
+        assert rel_l2(res[rid]["state"], alone[rid]["state"]) < 1e-12

@@ -12,11 +12,12 @@ from .mesh import (Mesh, structured_hex_mesh, warped_node_coords, BC_INTERIOR,
 from .material import smooth_random_material, homogeneous_material
 from .fields import plane_p_wave, gaussian_stress_pulse, random_state
 from .configs import parity_config, large_config, precision_config
+from .serving import Request, make_requests
 
 __all__ = [
     "Mesh", "structured_hex_mesh", "warped_node_coords", "rotate_elements",
     "BC_INTERIOR", "BC_FREE_SURFACE", "BC_ABSORBING",
     "smooth_random_material", "homogeneous_material",
     "plane_p_wave", "gaussian_stress_pulse", "random_state",
-    "parity_config", "large_config", "precision_config",
+    "parity_config", "large_config", "precision_config", "Request", "make_requests",
 ]
