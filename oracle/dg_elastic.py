@@ -287,6 +287,7 @@ class ElasticDG:
         self.w_vol = wv                                        # [Np]
         self.w_face = np.einsum("b,a->ba", self.w, self.w).ravel()   # [n^2], a fastest
         self.source = None
+        self.receivers = []
         self._geo_cache = {}
         self._nbr_cache = {}
         self._abs_cache = {}
@@ -400,21 +401,24 @@ class ElasticDG:
         return um, up
 
     # ---- the operator ----------------------------------------------------
-    def volume_term(self, u_e, Ja, J):
+    def volume_term(self, u_e, Ja, J, sign=1.0):
         """Split (skew-symmetric) strong form of -sum_k d_k(A_k u):
-        -1/2 [ 1/J sum_i d_i(sum_k Ja^i_k A_k u) + 1/J sum_i sum_k Ja^i_k A_k d_i u ]."""
-        Au = [np.einsum("pq,qen->pen", A_K[k], u_e) for k in range(3)]
+        -1/2 [ 1/J sum_i d_i(sum_k Ja^i_k A_k u) + 1/J sum_i sum_k Ja^i_k A_k d_i u ].
+        sign = -1 evaluates the same form with A_k replaced by -A_k."""
+        Ak = [sign * A_K[k] for k in range(3)]
+        Au = [np.einsum("pq,qen->pen", Ak[k], u_e) for k in range(3)]
         cons = np.zeros_like(u_e)
         noncons = np.zeros_like(u_e)
         for i in range(3):
             Ftilde = sum(Ja[i][k][None] * Au[k] for k in range(3))
             cons += self.dref(Ftilde, i)
             du = self.dref(u_e, i)
-            noncons += sum(Ja[i][k][None] * np.einsum("pq,qen->pen", A_K[k], du) for k in range(3))
+            noncons += sum(Ja[i][k][None] * np.einsum("pq,qen->pen", Ak[k], du) for k in range(3))
         return -0.5 * (cons + noncons) / J[None]
 
-    def surface_term(self, u, elems, Ja, J):
-        """Sum over faces of (w_f sJ)/(w_vol J) (F(u^-).n - F_hat.n) at the face nodes."""
+    def surface_term(self, u, elems, Ja, J, sign=1.0):
+        """Sum over faces of (w_f sJ)/(w_vol J) (F(u^-).n - F_hat.n) at the face nodes.
+        sign = -1: flux matrices A(n) replaced by -A(n), stabilisation unchanged."""
         out = np.zeros((NFIELD, len(elems), self.Np))
         for f in range(6):
             fn = self.face_nodes[f]
@@ -424,7 +428,7 @@ class ElasticDG:
             um, up = self.exterior_state(u, elems, f)
             um = np.moveaxis(um, 0, -1)                        # [ne, nf, 9]
             up = np.moveaxis(up, 0, -1)
-            An = np.einsum("...k,kij->...ij", nrm, A_STACK)
+            An = sign * np.einsum("...k,kij->...ij", nrm, A_STACK)
             stab = self.tau * self._abs_A_cached(elems, f, nrm)
             s_uhat = weighted_trace(An, stab, um, up)
             Fhat = hdg_flux(An, stab, um, s_uhat)
@@ -451,21 +455,135 @@ class ElasticDG:
         s[:3] = F[:, None] * float(ricker(t, f0, t0)) * l3[None, :] / (self.w_vol * J[0])[None, :]
         return e, s
 
-    def rhs(self, u, elems=None, t=0.0):
-        """L(u) = Q^{-1}[volume + surface + source] for the elements in elems (default all)."""
+    def rhs(self, u, elems=None, t=0.0, sign=1.0, source=True):
+        """L(u) = Q^{-1}[volume + surface + source] for the elements in elems (default all).
+        sign = -1 gives the reversed operator L_rev (A_k -> -A_k, same stabilisation)."""
         u = np.asarray(u, dtype=np.float64)
         elems = np.arange(self.nel) if elems is None else np.asarray(elems, dtype=np.int64)
         Ja, J = self.geometry(elems)
         if np.any(J <= 0.0):
             raise ValueError("non-positive Jacobian")
         u_e = u[:, elems]
-        r = self.volume_term(u_e, Ja, J) + self.surface_term(u, elems, Ja, J)
-        if self.source is not None:
+        r = self.volume_term(u_e, Ja, J, sign) + self.surface_term(u, elems, Ja, J, sign)
+        if source and self.source is not None:
             es, sn = self.source_nodal(t)
             hit = np.nonzero(elems == es)[0]
             if hit.size:
                 r[:, hit[0]] += sn
         return np.einsum("epq,qen->pen", self.Qinv(elems), r)
+
+    # ---- adjoint ---------------------------------------------------------
+    def mass_Q(self, u, inverse=False):
+        """Apply M Q (or its inverse) node by node: w J Q_e u (Q_e per element)."""
+        elems = np.arange(self.nel)
+        _, J = self.geometry(elems)
+        out = np.empty_like(u)
+        for e in elems:
+            Q = Q_of(self.rho[e], self.lam[e], self.mu[e])
+            wJ = self.w_vol * J[e]
+            if inverse:
+                out[:, e] = np.linalg.solve(Q, u[:, e]) / wJ[None, :]
+            else:
+                out[:, e] = (Q @ u[:, e]) * wJ[None, :]
+        return out
+
+    def rhs_adjoint(self, w):
+        """L^T w (Euclidean transpose of the linear part of L).  M Q L splits into a
+        part that is skew and linear in A (volume + central flux) and a symmetric
+        part independent of the sign of A (stabilisation), so
+        L^T = (M Q) L_rev (M Q)^{-1}, L_rev = L with A_k -> -A_k."""
+        return self.mass_Q(self.rhs(self.mass_Q(w, inverse=True), sign=-1.0, source=False))
+
+    def adjoint_stage(self, lu, lr, s, dt):
+        """Transpose of the stage map (u, res) -> (u + b_s res', res'),
+        res' = a_s res + dt L u:  w = b_s lu + lr;  lu <- lu + dt L^T w;  lr <- a_s w."""
+        a, b = float(LSRK_A[s]), float(LSRK_B[s])
+        w = b * lu + lr
+        return lu + dt * self.rhs_adjoint(w), a * w
+
+    def adjoint_step(self, lu, lr, dt):
+        for s in reversed(range(5)):
+            lu, lr = self.adjoint_stage(lu, lr, s, dt)
+        return lu, lr
+
+    # ---- receivers --------------------------------------------------------
+    def set_receivers(self, elems, xis):
+        self.receivers = [(int(e), np.asarray(x, dtype=np.float64)) for e, x in zip(elems, xis)]
+
+    def _receiver_basis(self, xi):
+        li = [lagrange_values(self.r, xi[a]) for a in range(3)]
+        return np.einsum("k,j,i->kji", li[2], li[1], li[0]).ravel()
+
+    def sample_receivers(self, u):
+        """Velocity at the receivers: sum_j l_j(xi_r) v_j over the receiver's element."""
+        return np.array([u[:3, e] @ self._receiver_basis(xi) for e, xi in self.receivers])
+
+    def receivers_adjoint(self, g):
+        """Transpose of sample_receivers: g [nrec, 3] -> a state-shaped array."""
+        out = np.zeros((NFIELD, self.nel, self.Np))
+        for (e, xi), gr in zip(self.receivers, g):
+            out[:3, e] += gr[:, None] * self._receiver_basis(xi)[None, :]
+        return out
+
+    # ---- misfit and material gradient (small problems) --------------------
+    def forward_traces(self, u0, dt, nsteps, t0=0.0):
+        """States at step starts and receiver traces after each step."""
+        u, res = u0.copy(), np.zeros_like(u0)
+        starts, traces = [], []
+        for k in range(nsteps):
+            starts.append(u.copy())
+            u, res = self.step(u, res, dt, t=t0 + k * dt)
+            traces.append(self.sample_receivers(u))
+        return starts, np.array(traces)
+
+    def misfit(self, traces, data, dt):
+        """J = 1/2 dt sum_n sum_r |v_r(t_n) - d_r(t_n)|^2."""
+        return 0.5 * dt * float(np.sum((traces - data) ** 2))
+
+    def dL_dm(self, u, e, p, h_rel=1e-6):
+        """(dL/dm) u for parameter p in {0: rho, 1: lam, 2: mu} of element e, by a
+        central difference of the operator in that parameter (the operator is
+        smooth in the medium); only e and its neighbours change."""
+        vals = [self.rho, self.lam, self.mu]
+        base = vals[p][e]
+        h = h_rel * abs(base)
+        nb = sorted({int(e)} | {int(x) for x in self.etoe[e] if x >= 0})
+        elems = np.array(nb)
+        out = []
+        for sgn in (1.0, -1.0):
+            vals[p][e] = base + sgn * h
+            self._abs_cache.clear()
+            self._qinv_cache.clear()
+            out.append(self.rhs(u, elems, source=False))
+        vals[p][e] = base
+        self._abs_cache.clear()
+        self._qinv_cache.clear()
+        return elems, (out[0] - out[1]) / (2 * h)
+
+    def gradient(self, u0, data, dt, nsteps, elems_params, t0=0.0):
+        """dJ/dm for the listed (element, parameter) pairs by the discrete adjoint:
+        backward over steps and stages, with the stage inputs recomputed from the
+        step starts, accumulating dt w_s^T (dL/dm) u_{s-1}."""
+        starts, traces = self.forward_traces(u0, dt, nsteps, t0)
+        lu = np.zeros_like(u0)
+        lr = np.zeros_like(u0)
+        grad = np.zeros(len(elems_params))
+        for k in reversed(range(nsteps)):
+            lu = lu + self.receivers_adjoint(dt * (traces[k] - data[k]))
+            # stage inputs of step k
+            u, res = starts[k].copy(), np.zeros_like(u0)
+            ins = []
+            for s in range(5):
+                ins.append(u)
+                u, res = self.lsrk_stage(u, res, s, dt, t=t0 + k * dt)
+            for s in reversed(range(5)):
+                a, b = float(LSRK_A[s]), float(LSRK_B[s])
+                w = b * lu + lr
+                for i, (e, p) in enumerate(elems_params):
+                    el, d = self.dL_dm(ins[s], e, p)
+                    grad[i] += dt * float(np.sum(w[:, el] * d))
+                lu, lr = lu + dt * self.rhs_adjoint(w), a * w
+        return grad
 
     # ---- time stepping ---------------------------------------------------
     def lsrk_stage(self, u, res, s, dt, elems=None, t=0.0):

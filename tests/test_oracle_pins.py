@@ -492,3 +492,97 @@ def test_point_source_total_force_and_location():
     _, sn2 = op.source_nodal(t)
     node = 1 + 5 * (0 + 5 * 3)
     assert np.count_nonzero(np.abs(sn2[0]) > 1e-14) == 1 and sn2[0, node] != 0
+
+
+# ------------------------------------------------------------------ adjoint
+def _bc_operator(E, N, mat, rotate=None):
+    return _operator(E, N, 0.08, periodic=(True, False, False),
+                     boundary={2: wl.BC_FREE_SURFACE, 3: wl.BC_ABSORBING, 4: wl.BC_ABSORBING,
+                               5: wl.BC_FREE_SURFACE}, mat=mat, rotate=rotate)
+
+
+def test_adjoint_rhs_is_the_bruteforce_transpose():
+    op, mesh, x = _bc_operator(1, 1, 21)
+    n = 9 * op.nel * op.Np
+    L = np.zeros((n, n))
+    LT = np.zeros((n, n))
+    for c in range(n):
+        e = np.zeros(n)
+        e[c] = 1.0
+        L[:, c] = op.rhs(e.reshape(9, op.nel, op.Np)).ravel()
+        LT[:, c] = op.rhs_adjoint(e.reshape(9, op.nel, op.Np)).ravel()
+    np.testing.assert_allclose(LT, L.T, atol=1e-12 * np.max(np.abs(L)))
+
+
+@pytest.mark.parametrize("rotate", [None, 5])
+def test_adjoint_dot_products(rotate):
+    op, mesh, x = _bc_operator(2, 3, 22, rotate)
+    rng = np.random.default_rng(3)
+    v = rng.standard_normal((9, op.nel, op.Np))
+    w = rng.standard_normal((9, op.nel, op.Np))
+    a, b = np.sum(w * op.rhs(v)), np.sum(op.rhs_adjoint(w) * v)
+    assert abs(a - b) <= 1e-12 * abs(a)
+    # one LSRK step as a linear map of (u, res)
+    dt = 1e-3
+    du, dr = rng.standard_normal((2, 9, op.nel, op.Np))
+    lu, lr = rng.standard_normal((2, 9, op.nel, op.Np))
+    u1, r1 = op.step(du, dr, dt)
+    au, ar = op.adjoint_step(lu, lr, dt)
+    lhs = np.sum(lu * u1) + np.sum(lr * r1)
+    rhs = np.sum(au * du) + np.sum(ar * dr)
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def test_receivers_sample_exactly_and_transpose():
+    op, mesh, x = _bc_operator(2, 3, 23)
+    rng = np.random.default_rng(4)
+    xis = rng.uniform(-1, 1, (5, 3))
+    xis[0] = [op.r[1], op.r[2], op.r[0]]                 # a receiver on a node
+    op.set_receivers([0, 3, 5, 7, 2], xis)
+    # a velocity field that is a polynomial of degree <= N in the reference coords
+    rr = wl.mesh.reference_grid(op.r)
+    u = np.zeros((9, op.nel, op.Np))
+    poly = lambda p: p[..., 0] ** 3 - 2 * p[..., 1] * p[..., 2] + 0.5
+    u[0] = poly(rr)[None, :]
+    s = op.sample_receivers(u)
+    np.testing.assert_allclose(s[:, 0], poly(xis), atol=1e-13)
+    assert s[0, 0] == u[0, 0, 1 + 4 * (2 + 4 * 0)]
+    g = rng.standard_normal((5, 3))
+    v = rng.standard_normal((9, op.nel, op.Np))
+    assert abs(np.sum(g * op.sample_receivers(v)) - np.sum(op.receivers_adjoint(g) * v)) < 1e-12
+
+
+def test_adjoint_gradient_matches_finite_differences():
+    op, mesh, x = _bc_operator(2, 2, 24)
+    op.set_receivers([1, 6], [[0.1, -0.2, 0.3], [-0.4, 0.5, 0.0]])
+    op.set_point_force(3, [0.2, 0.1, -0.3], [0.3, -0.5, 1.0], 4.0, 0.05)
+    u0 = np.zeros((9, op.nel, op.Np))
+    dt, nsteps = 0.02, 6
+    # data: traces of a run with a perturbed medium
+    saved = [v.copy() for v in (op.rho, op.lam, op.mu)]
+    op.rho *= 1.05
+    op.mu *= 0.97
+    op._abs_cache.clear()
+    op._qinv_cache.clear()
+    _, data = op.forward_traces(u0, dt, nsteps)
+    op.rho[:], op.lam[:], op.mu[:] = saved
+    op._abs_cache.clear()
+    op._qinv_cache.clear()
+    pairs = [(0, 0), (3, 1), (5, 2), (6, 0)]
+    grad = op.gradient(u0, data, dt, nsteps, pairs)
+    vals = [op.rho, op.lam, op.mu]
+    for (e, p), g in zip(pairs, grad):
+        base = vals[p][e]
+        h = 1e-5 * abs(base)
+        J = []
+        for sgn in (1.0, -1.0):
+            vals[p][e] = base + sgn * h
+            op._abs_cache.clear()
+            op._qinv_cache.clear()
+            _, tr = op.forward_traces(u0, dt, nsteps)
+            J.append(op.misfit(tr, data, dt))
+        vals[p][e] = base
+        op._abs_cache.clear()
+        op._qinv_cache.clear()
+        fd = (J[0] - J[1]) / (2 * h)
+        assert abs(g - fd) <= 1e-6 * abs(fd), (e, p, g, fd)
