@@ -540,10 +540,11 @@ class ElasticDG:
         """J = 1/2 dt sum_n sum_r |v_r(t_n) - d_r(t_n)|^2."""
         return 0.5 * dt * float(np.sum((traces - data) ** 2))
 
-    def dL_dm(self, u, e, p, h_rel=1e-6):
-        """(dL/dm) u for parameter p in {0: rho, 1: lam, 2: mu} of element e, by a
-        central difference of the operator in that parameter (the operator is
-        smooth in the medium); only e and its neighbours change."""
+    def dL_dm(self, u, e, p, t=0.0, h_rel=1e-6):
+        """d/dm of the stage right-hand side L(u) + Q^{-1} f(t) for parameter p in
+        {0: rho, 1: lam, 2: mu} of element e, by a central difference in that
+        parameter (the operator is smooth in the medium; the point force enters
+        through Q^{-1}); only e and its neighbours change."""
         vals = [self.rho, self.lam, self.mu]
         base = vals[p][e]
         h = h_rel * abs(base)
@@ -554,7 +555,7 @@ class ElasticDG:
             vals[p][e] = base + sgn * h
             self._abs_cache.clear()
             self._qinv_cache.clear()
-            out.append(self.rhs(u, elems, source=False))
+            out.append(self.rhs(u, elems, t=t))
         vals[p][e] = base
         self._abs_cache.clear()
         self._qinv_cache.clear()
@@ -579,8 +580,9 @@ class ElasticDG:
             for s in reversed(range(5)):
                 a, b = float(LSRK_A[s]), float(LSRK_B[s])
                 w = b * lu + lr
+                ts = t0 + k * dt + float(LSRK_C[s]) * dt
                 for i, (e, p) in enumerate(elems_params):
-                    el, d = self.dL_dm(ins[s], e, p)
+                    el, d = self.dL_dm(ins[s], e, p, ts)
                     grad[i] += dt * float(np.sum(w[:, el] * d))
                 lu, lr = lu + dt * self.rhs_adjoint(w), a * w
         return grad

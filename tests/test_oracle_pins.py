@@ -568,7 +568,7 @@ def test_adjoint_gradient_matches_finite_differences():
     op.rho[:], op.lam[:], op.mu[:] = saved
     op._abs_cache.clear()
     op._qinv_cache.clear()
-    pairs = [(0, 0), (3, 1), (5, 2), (6, 0)]
+    pairs = [(0, 0), (3, 0), (3, 1), (5, 2), (6, 0)]     # (3, rho): the point force's element
     grad = op.gradient(u0, data, dt, nsteps, pairs)
     vals = [op.rho, op.lam, op.mu]
     for (e, p), g in zip(pairs, grad):
