@@ -64,7 +64,7 @@ typedef struct {
 } dgw_config;
 
 /* ABI version of this header (bumped on any signature change). */
-#define DGW_ABI_VERSION 4
+#define DGW_ABI_VERSION 5
 int dgw_abi_version(void);
 
 /* GLL nodes r[0..N] (ascending, r[0] = -1, r[N] = +1) and weights w[0..N]
@@ -159,10 +159,31 @@ dgw_status dgw_energy(dgw_ctx* ctx, const double* u, double* energy_out, void* s
 dgw_status dgw_source_set(dgw_ctx* ctx, int64_t element, const double* xi, const double* force, double f0,
                           double t0);
 
-/* Adjoint of dgw_step with material gradients.  Not built yet: returns
- * DGW_ERR_UNSUPPORTED. */
-dgw_status dgw_adjoint_step(dgw_ctx* ctx, double* lam_u, double* lam_res, double* grad_mat,
-                            const double* u_ckpt, double t0, double dt, int nsteps, void* stream);
+/* Adjoint of nsteps LSRK steps of size dt that start at time t0 from the
+ * forward state u_ckpt (device [9][nel][Np]; the register at a step start is
+ * irrelevant, a_0 = 0).  lam_u, lam_res (device, distinct): the adjoint state
+ * after the steps on entry, at t0 on return.  grad_mat (device [3][nel]:
+ * rho, lambda, mu per element) is incremented by sum over stages of
+ * dt w_s^T (dL/dm) u_{s-1} -- the contribution of these steps to the
+ * gradient of any functional of the states -- including the medium's effect
+ * on Q^{-1}, on the face impedances of the stabilisation and on the point
+ * force.  The transpose uses L^T = (M Q) L_rev (M Q)^{-1}, L_rev the operator
+ * with A_k -> -A_k (the upwind stabilisation of eq. RiemannFluxBoth is
+ * symmetric and unchanged).  Stage inputs are recomputed from u_ckpt.  Adjoint
+ * sources between steps (dgw_receivers_adjoint) need nsteps = 1 per call.
+ * FP64 contexts only (DGW_ERR_UNSUPPORTED otherwise). */
+dgw_status dgw_adjoint_step(dgw_ctx* ctx, double* lam_u, double* lam_res, double* grad_mat, const double* u_ckpt,
+                            double t0, double dt, int nsteps, void* stream);
+
+/* Receivers: velocity sampled at reference points xi[n][3] of elements[n]
+ * (host arrays) with the element's Lagrange basis.  n = 0 removes them. */
+dgw_status dgw_receivers_set(dgw_ctx* ctx, int n, const int64_t* elements, const double* xi);
+
+/* out[n][3] (device) = velocity of u (device) at the receivers. */
+dgw_status dgw_receivers_sample(dgw_ctx* ctx, const double* u, double* out, void* stream);
+
+/* Transpose of dgw_receivers_sample: lam_u (device state) += S^T g, g device [n][3]. */
+dgw_status dgw_receivers_adjoint(dgw_ctx* ctx, double* lam_u, const double* g, void* stream);
 
 /* dt = cfl * h / (c_max * N^2) with h the smallest element edge length
  * (distance between adjacent element corner nodes) and c_max the largest

@@ -44,6 +44,9 @@ SIGNATURES = {
     "dgw_step": (_I, [_P, _P, _P, _D, _D, _I, _P]),
     "dgw_energy": (_I, [_P, _P, ctypes.POINTER(_D), _P]),
     "dgw_source_set": (_I, [_P, _I64, _P, _P, _D, _D]),
+    "dgw_receivers_set": (_I, [_P, _I, _P, _P]),
+    "dgw_receivers_sample": (_I, [_P, _P, _P, _P]),
+    "dgw_receivers_adjoint": (_I, [_P, _P, _P, _P]),
     "dgw_adjoint_step": (_I, [_P, _P, _P, _P, _P, _D, _D, _I, _P]),
     "dgw_dt_cfl": (_I, [_P, ctypes.POINTER(_D)]),
     "dgw_batch_create": (_I, [ctypes.POINTER(_P), _I, _I, _I, _I]),
@@ -141,6 +144,18 @@ def dgw_energy(ctx, u, stream):
 
 def dgw_source_set(ctx, element, xi, force, f0, t0):
     return load().dgw_source_set(ctx, element, xi, force, f0, t0)
+
+
+def dgw_receivers_set(ctx, n, elements, xi):
+    return load().dgw_receivers_set(ctx, n, elements, xi)
+
+
+def dgw_receivers_sample(ctx, u, out, stream):
+    return load().dgw_receivers_sample(ctx, u, out, stream)
+
+
+def dgw_receivers_adjoint(ctx, lam_u, g, stream):
+    return load().dgw_receivers_adjoint(ctx, lam_u, g, stream)
 
 
 def dgw_adjoint_step(ctx, lam_u, lam_res, grad_mat, u_ckpt, t0, dt, nsteps, stream):

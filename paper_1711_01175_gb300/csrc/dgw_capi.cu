@@ -67,6 +67,15 @@ void free_mesh(dgw_ctx* c) {
   dfree(c->ec);
   dfree(c->src_w);
   c->src_elem = -1;
+  dfree(c->rec_elem);
+  dfree(c->rec_w);
+  c->rec_n = 0;
+  dfree(c->adj_scratch);
+  c->adj_scratch_bytes = 0;
+  dfree(c->adj_gface);
+  c->adj_gface_bytes = 0;
+  dfree(c->etoe_d);
+  dfree(c->etof_d);
   c->has_mesh = c->has_material = false;
   c->nel = 0;
 }
@@ -422,6 +431,7 @@ dgw_status dgw_mesh_upload(dgw_ctx* c, int64_t nel, const double* x, const int64
 #undef DGW_TRY
   c->nel = nel;
   c->etoe.assign(etoe, etoe + nel * 6);
+  c->etof.assign(etof, etof + nel * 6);
   c->bc.assign(bc, bc + nel * 6);
   c->h_min = hmin;
   c->has_mesh = true;
@@ -669,9 +679,6 @@ dgw_status dgw_source_set(dgw_ctx* c, int64_t element, const double* xi, const d
   return DGW_OK;
 }
 
-dgw_status dgw_adjoint_step(dgw_ctx* c, double*, double*, double*, const double*, double, double, int, void*) {
-  return fail(c, DGW_ERR_UNSUPPORTED, "adjoint_step is not built");
-}
 
 dgw_status dgw_dt_cfl(dgw_ctx* c, double* dt_out) {
   dgw_status st = ready(c);

@@ -59,6 +59,8 @@ struct StageParams {
   const double* wJ;         // [nel][Np] (with energy_partials)
   const double* ec;         // [4][nel] energy constants (with energy_partials)
   long long pf_elems;       // L2 prefetch distance in elements (0: off)
+  double* grad_el;          // GRAD mode: [3][nel] element terms (accumulated)
+  double* grad_face;        // GRAD mode: [2][nel*6*nf] face-node terms for Zs, Zp (accumulated)
   long long src_elem;       // element holding the point force, -1 for none
   double src_amp;           // Ricker amplitude R(t + c_s dt) of this stage
   const double* src_w;      // [3][Np]: F_q l_j(xi_s) / (rho w_j J_j)
@@ -101,6 +103,7 @@ cudaError_t launch_stage_batch(int N, bool mixed, const BatchLaunch& L, int grid
 cudaError_t prepare_stage_batch(int N, bool mixed, int sm_count, int* grid);
 cudaError_t launch_stage_fp64(int N, bool lsrk, const StageParams& p, cudaStream_t s);
 cudaError_t launch_stage_mixed(int N, bool lsrk, const StageParams& p, cudaStream_t s);
+cudaError_t launch_stage_adjoint(int N, int mode, const StageParams& p, cudaStream_t s);   // mode 2: ADJ, 3: GRAD
 void stage_shape(int N, int* epb, int* threads);
 
 // Geometry (dgw_geometry.cu).
@@ -152,7 +155,18 @@ struct dgw_ctx {
   long long src_elem = -1;
   double src_f0 = 0.0, src_t0 = 0.0;
   std::vector<int64_t> etoe;   // host copy of the connectivity (face media)
+  std::vector<int8_t> etof;
   std::vector<int8_t> bc;
+  // receivers and adjoint scratch
+  int rec_n = 0;
+  long long* rec_elem = nullptr;     // [rec_n]
+  double* rec_w = nullptr;           // [rec_n][Np] Lagrange basis at the receiver
+  double* adj_scratch = nullptr;
+  size_t adj_scratch_bytes = 0;
+  double* adj_gface = nullptr;
+  size_t adj_gface_bytes = 0;
+  long long* etoe_d = nullptr;
+  signed char* etof_d = nullptr;
   double h_min = 0.0;
   double c_max = 0.0;
   std::string err;

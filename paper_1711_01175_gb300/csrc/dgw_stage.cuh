@@ -139,10 +139,20 @@ struct StageSmem {
   static constexpr size_t bytes = r_off + (kPrefetchRes ? sizeof(double) * 9 * S::NTILE : 0);
 };
 
+// Kernel modes.  RHS: write L(u).  LSRK: fused 2N-storage stage update.
+// ADJ: the reversed operator (A_k -> -A_k, same stabilisation) without Q^{-1}
+//   on a prepared adjoint weight z = (M Q)^{-1} w, and lu <- lu + dt w J r,
+//   which together apply dt L^T w (L^T = (M Q) L_rev (M Q)^{-1}).
+// GRAD: the forward operator on a stage input u, accumulating the material
+//   gradient terms dt w^T (dL/dm) u of the adjoint weight w.
+enum { kModeRhs = 0, kModeLsrk = 1, kModeAdj = 2, kModeGrad = 3 };
+
 // One tile (EPB consecutive elements) of one solve.  The caller has filled the
 // D tile of shared memory; p may live in parameter or shared memory.
-template <int N, typename Real, bool LSRK>
+template <int N, typename Real, int MODE>
 __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile, unsigned char* smem_raw) {
+  constexpr bool LSRK = MODE == kModeLsrk;
+  const Real sgnA = MODE == kModeAdj ? Real(-1) : Real(1);
   using S = Shape<N>;
   using L = StageSmem<N, Real>;
   using V = Pack<Real>;
@@ -346,10 +356,50 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
                             m2 * z2 + m3 * z1, m1 * z2 + m3 * z0, m1 * z1 + m2 * z0};
         // 1/2 (A(m) - tau S(m)) du (1/J)/w_0 = -1/2 (A_+ du + tau S du) (1/J)/w_0
 #pragma unroll
-        for (int q = 0; q < 9; ++q) flux[q] = s * (Ad[q] + tau * Sd[q]);
+        for (int q = 0; q < 9; ++q) flux[q] = s * (sgnA * Ad[q] + tau * Sd[q]);
+        if constexpr (MODE == kModeGrad) {
+          // d(flux)/dZs and d(flux)/dZp against Q_e^{-1} w at this node.
+          const size_t gi = static_cast<size_t>(ei) * Np + vn;
+          const Real* matg = static_cast<const Real*>(p.mat);
+          const Real irho = matg[ei], lamg = matg[p.nel + ei], mug = matg[2 * p.nel + ei];
+          Real w[9], qh[9];
+#pragma unroll
+          for (int q = 0; q < 9; ++q) w[q] = p.res[q * fstride + gi];
+          qh[0] = irho * w[0];
+          qh[1] = irho * w[1];
+          qh[2] = irho * w[2];
+          const Real trw = w[3] + w[4] + w[5];
+          qh[3] = lamg * trw + 2 * mug * w[3];
+          qh[4] = lamg * trw + 2 * mug * w[4];
+          qh[5] = lamg * trw + 2 * mug * w[5];
+          qh[6] = mug * w[6];
+          qh[7] = mug * w[7];
+          qh[8] = mug * w[8];
+          Real zq[9], Bq[9];
+#pragma unroll
+          for (int q = 0; q < 3; ++q) zq[q] = 0;
+#pragma unroll
+          for (int q = 3; q < 9; ++q) zq[q] = qh[q];
+          apply_Apos(m1, m2, m3, zq, Bq);                 // Bq[0..2] = B(m)^T qh_sigma
+          const Real mdv = (m1 * du[0] + m2 * du[1] + m3 * du[2]) * isJ;
+          const Real mqv = (m1 * qh[0] + m2 * qh[1] + m3 * qh[2]) * isJ;
+          const Real my = (m1 * Ad[0] + m2 * Ad[1] + m3 * Ad[2]) * isJ;    // (n.y) sJ
+          const Real mbq = (m1 * Bq[0] + m2 * Bq[1] + m3 * Bq[2]) * isJ;
+          const Real yb = Ad[0] * Bq[0] + Ad[1] * Bq[1] + Ad[2] * Bq[2];
+          const Real qdv = qh[0] * du[0] + qh[1] * du[1] + qh[2] * du[2];
+          // velocity rows: dS/dZs = sJ (I - n n^T), dS/dZp = sJ n n^T
+          // stress rows:   dS/dZs = -(1/Zs^2) (1/sJ) B_m (I - n n^T) B_m^T, dS/dZp = -(1/Zp^2) (1/sJ) B_m n n^T B_m^T
+          const Real izp = izs + diz;
+          const Real gzs = sJ * (qdv - mdv * mqv) - izs * izs * isJ * (yb - my * mbq);
+          const Real gzp = sJ * mdv * mqv - izp * izp * isJ * my * mbq;
+          const size_t ii = static_cast<size_t>(ei) * 6 * nf + r;
+          const Real sc = static_cast<Real>(p.dt) * s * tau;
+          p.grad_face[ii] += sc * gzs;
+          p.grad_face[static_cast<size_t>(p.nel) * 6 * nf + ii] += sc * gzp;
+        }
       } else {
 #pragma unroll
-        for (int q = 0; q < 9; ++q) flux[q] = s * Ad[q];
+        for (int q = 0; q < 9; ++q) flux[q] = s * sgnA * Ad[q];
       }
 #pragma unroll
       for (int q = 0; q < 9; ++q) x_s[q * NFI + it] = flux[q];
@@ -358,12 +408,13 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
   __syncthreads();
 
   double e_node = 0.0;     // w J u_out^T Q u_out of this node (fused energy)
+  Real gnode[3] = {0, 0, 0};   // GRAD mode: this node's material gradient terms
   if (active) {
     // vol = -1/2 (1/J) (-acc_+) = +1/2 (1/J) acc_+  (acc holds A_+ terms)
     Real r[9];
     const Real hv = static_cast<Real>(0.5) * g_s[t * PK + 9];
 #pragma unroll
-    for (int q = 0; q < 9; ++q) r[q] = hv * acc[q];
+    for (int q = 0; q < 9; ++q) r[q] = hv * sgnA * acc[q];
     const int fb0 = el * 6 * nf;
     auto add_face = [&](int f, int pidx) {
 #pragma unroll
@@ -376,6 +427,30 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
     if (iz == 0) add_face(4, ix + n * iy);
     if (iz == N) add_face(5, ix + n * iy);
 
+    if constexpr (MODE == kModeAdj) {
+      // lu <- lu + dt (w J) r : M Q L_rev z without Q^{-1} (Q^{-1} and Q cancel)
+      const double wj = p.wJ[gidx];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) p.out[q * fstride + gidx] = p.res[q * fstride + gidx] + p.dt * wj * r[q];
+    }
+    if constexpr (MODE == kModeGrad) {
+      // dt w^T (d Q^{-1}/dm) (K u + f) at this node, f the point force (before Q^{-1})
+      const Real* matg = static_cast<const Real*>(p.mat);
+      const Real irho = matg[e];
+      if (e == p.src_elem) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) r[q] += static_cast<Real>(p.src_amp * p.src_w[q * Np + node]) / irho;
+      }
+      Real w[9];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) w[q] = p.res[q * fstride + gidx];
+      const Real dtg = static_cast<Real>(p.dt);
+      gnode[0] = -dtg * irho * irho * (w[0] * r[0] + w[1] * r[1] + w[2] * r[2]);
+      gnode[1] = dtg * (w[3] + w[4] + w[5]) * (r[3] + r[4] + r[5]);
+      gnode[2] = dtg * (2 * (w[3] * r[3] + w[4] * r[4] + w[5] * r[5]) + w[6] * r[6] + w[7] * r[7] + w[8] * r[8]);
+    }
+
+    if constexpr (MODE == kModeRhs || MODE == kModeLsrk) {
     // Q^{-1}: velocity rows / rho, stress rows by the isotropic stiffness C_V.
     const Real* mat = static_cast<const Real*>(p.mat);
     const Real irho = mat[e];
@@ -445,6 +520,25 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
         e_node = p.wJ[gidx] * (kin + pot);
       }
     }
+    }
+  }
+  if constexpr (MODE == kModeGrad) {
+    // Sum the node terms of each element in a fixed order (the state tile is free now).
+    __syncthreads();
+    if (in_tile) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) u_s[t * PK + c] = gnode[c];
+    }
+    __syncthreads();
+    if (t < 3 * EPB) {
+      const int ee = t / 3, c = t - 3 * (t / 3);
+      const long long eg = e0 + ee;
+      if (eg < p.nel) {
+        Real sum = 0;
+        for (int k = 0; k < Np; ++k) sum += u_s[(ee * Np + k) * PK + c];
+        p.grad_el[c * p.nel + eg] += sum;
+      }
+    }
   }
   if constexpr (LSRK) {
     if (p.energy_partials != nullptr) {
@@ -462,12 +556,12 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
   }
 }
 
-template <int N, typename Real, bool LSRK>
+template <int N, typename Real, int MODE>
 __global__ void __launch_bounds__(Shape<N>::NT) stage_kernel(const StageParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* D_s = reinterpret_cast<Real*>(smem_raw + StageSmem<N, Real>::d_off);
   for (int i = threadIdx.x; i < Shape<N>::n * Shape<N>::n; i += Shape<N>::NT) D_s[i] = static_cast<Real>(p.D[i]);
-  stage_tile<N, Real, LSRK>(p, blockIdx.x, smem_raw);
+  stage_tile<N, Real, MODE>(p, blockIdx.x, smem_raw);
 }
 
 __device__ __forceinline__ double ricker_dev(double t, double f0, double t0) {
@@ -518,7 +612,7 @@ __global__ void __launch_bounds__(Shape<N>::NT) stage_batch_kernel(const BatchLa
       local_tile = tile - b.tile0;
     }
     __syncthreads();
-    stage_tile<N, Real, true>(ps, local_tile, smem_raw);
+    stage_tile<N, Real, kModeLsrk>(ps, local_tile, smem_raw);
     __syncthreads();
   }
 }
@@ -573,19 +667,19 @@ cudaError_t prepare_stage_batch_any(int N, int sm_count, int* grid) {
   }
 }
 
-template <int N, typename Real, bool LSRK>
+template <int N, typename Real, int MODE>
 cudaError_t launch_stage_t(const StageParams& p, cudaStream_t s) {
   using S = Shape<N>;
   const size_t smem = StageSmem<N, Real>::bytes;
-  cudaError_t err = cudaFuncSetAttribute(stage_kernel<N, Real, LSRK>,
+  cudaError_t err = cudaFuncSetAttribute(stage_kernel<N, Real, MODE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  err = cudaFuncSetAttribute(stage_kernel<N, Real, LSRK>, cudaFuncAttributePreferredSharedMemoryCarveout,
+  err = cudaFuncSetAttribute(stage_kernel<N, Real, MODE>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
   if (err != cudaSuccess) return err;
   const long long blocks = (p.nel + S::EPB - 1) / S::EPB;
   if (blocks <= 0) return cudaSuccess;
-  stage_kernel<N, Real, LSRK><<<(unsigned)blocks, S::NT, smem, s>>>(p);
+  stage_kernel<N, Real, MODE><<<(unsigned)blocks, S::NT, smem, s>>>(p);
   return cudaGetLastError();
 }
 
@@ -593,7 +687,7 @@ template <typename Real>
 cudaError_t launch_stage_any(int N, bool lsrk, const StageParams& p, cudaStream_t s) {
 #define DGW_CASE(NN)                                                                   \
   case NN:                                                                             \
-    return lsrk ? launch_stage_t<NN, Real, true>(p, s) : launch_stage_t<NN, Real, false>(p, s);
+    return lsrk ? launch_stage_t<NN, Real, kModeLsrk>(p, s) : launch_stage_t<NN, Real, kModeRhs>(p, s);
   switch (N) {
     DGW_CASE(1)
     DGW_CASE(2)
@@ -606,6 +700,19 @@ cudaError_t launch_stage_any(int N, bool lsrk, const StageParams& p, cudaStream_
       return cudaErrorInvalidValue;
   }
 #undef DGW_CASE
+}
+
+// Adjoint modes (FP64 only).
+inline cudaError_t launch_stage_adjoint_any(int N, int mode, const StageParams& p, cudaStream_t s) {
+#define DGW_ACASE(NN)                                                                                  \
+  case NN:                                                                                             \
+    return mode == kModeAdj ? launch_stage_t<NN, double, kModeAdj>(p, s) : launch_stage_t<NN, double, kModeGrad>(p, s);
+  switch (N) {
+    DGW_ACASE(1) DGW_ACASE(2) DGW_ACASE(3) DGW_ACASE(4) DGW_ACASE(5) DGW_ACASE(6) DGW_ACASE(7)
+#undef DGW_ACASE
+    default:
+      return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace dgw

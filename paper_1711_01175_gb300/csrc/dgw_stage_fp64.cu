@@ -22,6 +22,10 @@ void stage_shape(int N, int* epb, int* threads) {
   }
 }
 
+cudaError_t launch_stage_adjoint(int N, int mode, const StageParams& p, cudaStream_t s) {
+  return launch_stage_adjoint_any(N, mode, p, s);
+}
+
 cudaError_t launch_stage_batch_fp64(int N, const BatchLaunch& L, int grid, cudaStream_t s) {
   return launch_stage_batch_any<double>(N, L, grid, s);
 }

@@ -54,6 +54,7 @@ class Solver:
         capi.check(st)
         self._ctx = h
         self.nel = 0
+        self._source = None
 
     def close(self):
         if getattr(self, "_ctx", None):
@@ -88,6 +89,8 @@ class Solver:
             if a.shape != (self.nel,):
                 raise ValueError("material arrays must be [nel]")
         self._check(capi.dgw_material_upload(self._ctx, *[_ptr(a) for a in arrs]))
+        if self._source is not None:          # the point force depends on rho: set it again
+            self.set_point_force(**self._source)
 
     def _field_check(self, a, name):
         if self.nel == 0:
@@ -100,9 +103,11 @@ class Solver:
 
     def set_point_force(self, element: int, xi, force, f0: float, t0: float):
         """Ricker point force in `element` at reference point xi (element -1 clears)."""
-        xi = np.ascontiguousarray(xi, dtype=np.float64)
-        force = np.ascontiguousarray(force, dtype=np.float64)
-        self._check(capi.dgw_source_set(self._ctx, int(element), _ptr(xi), _ptr(force), float(f0), float(t0)))
+        xi_a = np.ascontiguousarray(xi, dtype=np.float64)
+        force_a = np.ascontiguousarray(force, dtype=np.float64)
+        self._check(capi.dgw_source_set(self._ctx, int(element), _ptr(xi_a), _ptr(force_a), float(f0), float(t0)))
+        self._source = None if int(element) < 0 else dict(element=int(element), xi=list(xi_a), force=list(force_a),
+                                                             f0=float(f0), t0=float(t0))
 
     def rhs(self, u, out, t: float = 0.0, stream=None):
         self._field_check(u, "u")
@@ -136,6 +141,25 @@ class Solver:
         st, val = capi.dgw_energy(self._ctx, _ptr(u), _stream_handle(stream))
         self._check(st)
         return val
+
+    def set_receivers(self, elements, xi):
+        el = np.ascontiguousarray(elements, dtype=np.int64)
+        xi = np.ascontiguousarray(xi, dtype=np.float64).reshape(-1, 3)
+        self._check(capi.dgw_receivers_set(self._ctx, int(el.size), _ptr(el), _ptr(xi)))
+        self.nrec = int(el.size)
+
+    def sample_receivers(self, u, out, stream=None):
+        """out [nrec, 3] (device) = receiver velocities of u (device)."""
+        self._check(capi.dgw_receivers_sample(self._ctx, _ptr(u), _ptr(out), _stream_handle(stream)))
+        return out
+
+    def receivers_adjoint(self, lam_u, g, stream=None):
+        self._check(capi.dgw_receivers_adjoint(self._ctx, _ptr(lam_u), _ptr(g), _stream_handle(stream)))
+
+    def adjoint_step(self, lam_u, lam_res, grad, u_ckpt, dt: float, nsteps: int = 1, t0: float = 0.0, stream=None):
+        """Adjoint of nsteps steps from u_ckpt at t0; grad [3, nel] is incremented."""
+        self._check(capi.dgw_adjoint_step(self._ctx, _ptr(lam_u), _ptr(lam_res), _ptr(grad), _ptr(u_ckpt),
+                                          float(t0), float(dt), int(nsteps), _stream_handle(stream)))
 
     def dt_cfl(self) -> float:
         st, val = capi.dgw_dt_cfl(self._ctx)

@@ -303,5 +303,5 @@ def test_call_order_and_argument_errors():
     with pytest.raises(DGWError, match="stage"):
         s.stage(u, torch.empty_like(u), torch.zeros_like(u), 5, 1e-3)
     from paper_1711_01175_gb300 import capi
-    assert capi.dgw_adjoint_step(s._ctx, None, None, None, None, 0.0, 0.1, 1, None) == -7
+    assert capi.dgw_adjoint_step(s._ctx, None, None, None, None, 0.0, 0.1, 1, None) == -1
     s.close()
