@@ -64,7 +64,7 @@ typedef struct {
 } dgw_config;
 
 /* ABI version of this header (bumped on any signature change). */
-#define DGW_ABI_VERSION 5
+#define DGW_ABI_VERSION 6
 int dgw_abi_version(void);
 
 /* GLL nodes r[0..N] (ascending, r[0] = -1, r[N] = +1) and weights w[0..N]
@@ -199,8 +199,10 @@ dgw_status dgw_dt_cfl(dgw_ctx* ctx, double* dt_out);
  * arithmetic per element is the one of dgw_stage. */
 typedef struct dgw_batch dgw_batch;
 
-/* Create an empty batch for degree N, precision and flux_tau on `device`. */
-dgw_status dgw_batch_create(dgw_batch** out, int device, int N, int precision, int flux_tau);
+/* Create an empty batch for degree N, precision and flux_tau on `device`,
+ * holding up to max_solves solves.  Records the CUDA graph of two LSRK steps
+ * once; the kernels read the batch composition from device memory. */
+dgw_status dgw_batch_create(dgw_batch** out, int device, int N, int precision, int flux_tau, int max_solves);
 
 /* Free the batch (not the contexts or buffers it referenced; NULL accepted). */
 dgw_status dgw_batch_destroy(dgw_batch* b);
@@ -210,10 +212,10 @@ dgw_status dgw_batch_destroy(dgw_batch* b);
  * [9][nel_i][Np], the state in and out and the LSRK register), step size
  * dt[i] and current time t0[i] (for the point force).  The context's second
  * state buffer serves as the stage ping-pong partner, so a context belongs to
- * at most one batch at a time.  Uploads the descriptors on `stream` (and
- * waits for it), then records a CUDA graph of two LSRK steps on a private
- * stream of the batch.  Call again whenever the set of solves changes,
- * passing each continuing solve's current time. */
+ * at most one batch at a time.  Enqueues the descriptor uploads on `stream`
+ * (ordered after earlier replays on that stream; no synchronisation, no new
+ * graph).  Call again whenever the set of solves changes, passing each
+ * continuing solve's current time.  DGW_ERR_ARG beyond max_solves. */
 dgw_status dgw_batch_set(dgw_batch* b, int n, dgw_ctx* const* ctxs, double* const* u, double* const* res,
                          const double* dt, const double* t0, void* stream);
 

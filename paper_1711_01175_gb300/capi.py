@@ -49,7 +49,7 @@ SIGNATURES = {
     "dgw_receivers_adjoint": (_I, [_P, _P, _P, _P]),
     "dgw_adjoint_step": (_I, [_P, _P, _P, _P, _P, _D, _D, _I, _P]),
     "dgw_dt_cfl": (_I, [_P, ctypes.POINTER(_D)]),
-    "dgw_batch_create": (_I, [ctypes.POINTER(_P), _I, _I, _I, _I]),
+    "dgw_batch_create": (_I, [ctypes.POINTER(_P), _I, _I, _I, _I, _I]),
     "dgw_batch_destroy": (_I, [_P]),
     "dgw_batch_set": (_I, [_P, _I, _P, _P, _P, _P, _P, _P]),
     "dgw_batch_run": (_I, [_P, _I, _P]),
@@ -168,9 +168,9 @@ def dgw_dt_cfl(ctx):
     return st, out.value
 
 
-def dgw_batch_create(device, N, precision, flux_tau):
+def dgw_batch_create(device, N, precision, flux_tau, max_solves=1024):
     h = _P()
-    st = load().dgw_batch_create(ctypes.byref(h), device, N, precision, flux_tau)
+    st = load().dgw_batch_create(ctypes.byref(h), device, N, precision, flux_tau, max_solves)
     return st, h
 
 

@@ -2,12 +2,14 @@
 //
 // A batch holds solves of one degree, precision and flux, each owned by its
 // own context (mesh, medium, source) with caller-owned state and register.
-// dgw_batch_set uploads one descriptor per solve and captures a CUDA graph of
-// two LSRK steps: ten launches of the persistent batched stage kernel (every
-// launch covers the tiles of all solves; the state alternates between the
-// caller's buffer and the context's second buffer and is back in the caller's
-// buffer after ten stages) and one launch that advances each solve's device
-// time by 2 dt.  dgw_batch_run replays the graph.
+// dgw_batch_create records a CUDA graph of two LSRK steps: ten launches of the
+// persistent batched stage kernel (every launch covers the tiles of all
+// solves; the state alternates between the caller's buffer and the context's
+// second buffer and is back in the caller's buffer after ten stages) and one
+// launch that advances each solve's device time by 2 dt.  The kernels read
+// the batch composition (descriptors, count, tile total) from device memory,
+// so dgw_batch_set only enqueues uploads on the caller's stream -- no new
+// recording, no synchronisation -- and dgw_batch_run replays the graph.
 #include <cmath>
 #include <string>
 #include <vector>
@@ -31,9 +33,9 @@ cudaError_t prepare_stage_batch(int N, bool mixed, int sm_count, int* grid) {
 
 namespace {
 
-__global__ void batch_advance_kernel(const BatchSolve* solves, int n, int nsteps) {
+__global__ void batch_advance_kernel(const BatchSolve* solves, const BatchHeader* hdr, int nsteps) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) *solves[i].t += nsteps * solves[i].dt;
+  if (i < hdr->nsolves) *solves[i].t += nsteps * solves[i].dt;
 }
 
 // LSRK(5,4) of Carpenter & Kennedy (1994), 2N-storage, five stages, fourth order.
@@ -57,9 +59,11 @@ struct dgw_batch {
   int grid = 0;
   int nsolves = 0;
   long long total_tiles = 0;
-  dgw::BatchSolve* d_solves = nullptr;
-  double* d_times = nullptr;
+  dgw::BatchSolve* d_solves = nullptr;   // [capacity]
+  dgw::BatchHeader* d_hdr = nullptr;
+  double* d_times = nullptr;             // [capacity]
   int capacity = 0;
+  std::vector<dgw::BatchSolve> h_solves;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaStream_t capture = nullptr;   // private stream the graph is recorded on
@@ -96,27 +100,80 @@ void drop_graph(dgw_batch* b) {
 
 extern "C" {
 
-dgw_status dgw_batch_create(dgw_batch** out, int device, int N, int precision, int flux_tau) {
+dgw_status dgw_batch_create(dgw_batch** out, int device, int N, int precision, int flux_tau, int max_solves) {
   if (!out) return bfail(nullptr, DGW_ERR_ARG, "null argument");
   *out = nullptr;
   if (N < 1 || N > dgw::kMaxN) return bfail(nullptr, DGW_ERR_ARG, "N outside 1..7");
   if (precision != DGW_PRECISION_FP64 && precision != DGW_PRECISION_MIXED)
     return bfail(nullptr, DGW_ERR_ARG, "unknown precision");
   if (flux_tau != 0 && flux_tau != 1) return bfail(nullptr, DGW_ERR_ARG, "flux_tau must be 0 or 1");
+  if (max_solves < 1 || max_solves > (1 << 20)) return bfail(nullptr, DGW_ERR_ARG, "max_solves outside 1..2^20");
   if (cudaSetDevice(device) != cudaSuccess) return bfail(nullptr, DGW_ERR_CUDA, "cudaSetDevice failed");
   dgw_batch* b = new dgw_batch();
   b->device = device;
   b->N = N;
   b->precision = precision;
   b->tau = flux_tau;
+  b->capacity = max_solves;
   cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, device);
-  cudaError_t e = dgw::prepare_stage_batch(N, precision == DGW_PRECISION_MIXED, b->sm_count, &b->grid);
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
-  if (e != cudaSuccess) {
+  auto bail = [&](dgw_status st, const std::string& msg) {
+    drop_graph(b);
+    if (b->d_solves) cudaFree(b->d_solves);
+    if (b->d_hdr) cudaFree(b->d_hdr);
+    if (b->d_times) cudaFree(b->d_times);
     if (b->capture) cudaStreamDestroy(b->capture);
     delete b;
-    return bfail(nullptr, DGW_ERR_CUDA, std::string("batch kernel set-up: ") + cudaGetErrorString(e));
+    return bfail(nullptr, st, msg);
+  };
+  cudaError_t e = dgw::prepare_stage_batch(N, precision == DGW_PRECISION_MIXED, b->sm_count, &b->grid);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return bail(DGW_ERR_CUDA, std::string("batch kernel set-up: ") + cudaGetErrorString(e));
+  if (cudaMalloc(&b->d_solves, max_solves * sizeof(dgw::BatchSolve)) != cudaSuccess ||
+      cudaMalloc(&b->d_hdr, sizeof(dgw::BatchHeader)) != cudaSuccess ||
+      cudaMalloc(&b->d_times, max_solves * sizeof(double)) != cudaSuccess)
+    return bail(DGW_ERR_OOM, "batch descriptors");
+  dgw::BatchHeader h0{0, 0};
+  if (cudaMemcpyAsync(b->d_hdr, &h0, sizeof(h0), cudaMemcpyHostToDevice, b->capture) != cudaSuccess ||
+      cudaStreamSynchronize(b->capture) != cudaSuccess)
+    return bail(DGW_ERR_CUDA, "batch header");
+  // Record two LSRK steps once; the kernels read the composition from device memory.
+  int epb = 0, nt = 0;
+  dgw::stage_shape(N, &epb, &nt);
+  dgw::BatchLaunch L{};
+  L.solves = b->d_solves;
+  L.hdr = b->d_hdr;
+  L.tau = flux_tau ? 1.0 : 0.0;
+  dgw::RefElem R;
+  dgw::build_ref_elem(N, &R);
+  L.w_end_inv = 1.0 / R.w[0];
+  for (int i = 0; i < (N + 1) * (N + 1); ++i) L.D[i] = R.D[i];
+  L.pf_elems = 2LL * b->sm_count * epb;
+  cudaStream_t cs = b->capture;
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return bail(DGW_ERR_CUDA, std::string("begin capture: ") + cudaGetErrorString(e));
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    for (int st = 0; st < 5 && e == cudaSuccess; ++st) {
+      L.parity = (5 * k + st) & 1;
+      L.step = k;
+      L.a = dgw::kA[st];
+      L.b = dgw::kB[st];
+      L.c = dgw::kC[st];
+      e = dgw::launch_stage_batch(N, precision == DGW_PRECISION_MIXED, L, b->grid, cs);
+    }
   }
+  if (e == cudaSuccess) {
+    dgw::batch_advance_kernel<<<(max_solves + 127) / 128, 128, 0, cs>>>(b->d_solves, b->d_hdr, 2);
+    e = cudaGetLastError();
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return bail(DGW_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+  }
+  b->graph = g;
+  e = cudaGraphInstantiate(&b->exec, g, 0);
+  if (e != cudaSuccess) return bail(DGW_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e));
   *out = b;
   return DGW_OK;
 }
@@ -126,6 +183,7 @@ dgw_status dgw_batch_destroy(dgw_batch* b) {
   cudaSetDevice(b->device);
   drop_graph(b);
   if (b->d_solves) cudaFree(b->d_solves);
+  if (b->d_hdr) cudaFree(b->d_hdr);
   if (b->d_times) cudaFree(b->d_times);
   if (b->capture) cudaStreamDestroy(b->capture);
   delete b;
@@ -167,72 +225,20 @@ dgw_status dgw_batch_set(dgw_batch* b, int n, dgw_ctx* const* ctxs, double* cons
     d.tile0 = tiles;
     tiles += (c->nel + epb - 1) / epb;
   }
-  drop_graph(b);
+  if (n > b->capacity) return bfail(b, DGW_ERR_ARG, "more solves than the batch capacity");
+  for (int i = 0; i < n; ++i) hs[i].t = b->d_times + i;
+  // Stream-ordered uploads: earlier replays on this stream finish first.  The
+  // host copies live in the batch until the next set (pageable sources are
+  // staged by the runtime before the call returns).
+  b->h_solves = hs;
+  dgw::BatchHeader hdr{n, tiles};
+  if ((n > 0 && cudaMemcpyAsync(b->d_solves, b->h_solves.data(), n * sizeof(dgw::BatchSolve), cudaMemcpyHostToDevice,
+                                s) != cudaSuccess) ||
+      (n > 0 && cudaMemcpyAsync(b->d_times, t0, n * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess) ||
+      cudaMemcpyAsync(b->d_hdr, &hdr, sizeof(hdr), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return bfail(b, DGW_ERR_CUDA, "upload batch descriptors");
   b->nsolves = n;
   b->total_tiles = tiles;
-  if (n == 0) return DGW_OK;
-  if (n > b->capacity) {
-    if (b->d_solves) cudaFree(b->d_solves);
-    if (b->d_times) cudaFree(b->d_times);
-    b->d_solves = nullptr;
-    b->d_times = nullptr;
-    const int cap = n < 16 ? 16 : 2 * n;
-    if (cudaMalloc(&b->d_solves, cap * sizeof(dgw::BatchSolve)) != cudaSuccess ||
-        cudaMalloc(&b->d_times, cap * sizeof(double)) != cudaSuccess) {
-      b->capacity = 0;
-      return bfail(b, DGW_ERR_OOM, "batch descriptors");
-    }
-    b->capacity = cap;
-  }
-  for (int i = 0; i < n; ++i) hs[i].t = b->d_times + i;
-  if (cudaMemcpyAsync(b->d_solves, hs.data(), n * sizeof(dgw::BatchSolve), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemcpyAsync(b->d_times, t0, n * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess)
-    return bfail(b, DGW_ERR_CUDA, "upload batch descriptors");
-
-  // Capture two LSRK steps.
-  dgw::BatchLaunch L{};
-  L.solves = b->d_solves;
-  L.nsolves = n;
-  L.total_tiles = tiles;
-  L.tau = b->tau ? 1.0 : 0.0;
-  dgw::RefElem R;
-  dgw::build_ref_elem(b->N, &R);
-  L.w_end_inv = 1.0 / R.w[0];
-  for (int i = 0; i < (b->N + 1) * (b->N + 1); ++i) L.D[i] = R.D[i];
-  L.pf_elems = 2LL * b->sm_count * epb;
-  const int grid = (int)(tiles < b->grid ? tiles : b->grid);
-  // Recorded on the private stream (the caller's may be the legacy default
-  // stream, which cannot be captured); replays go to the caller's stream.
-  cudaStream_t cs = b->capture;
-  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-  if (e != cudaSuccess) return bfail(b, DGW_ERR_CUDA, std::string("begin capture: ") + cudaGetErrorString(e));
-  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
-    for (int st = 0; st < 5 && e == cudaSuccess; ++st) {
-      L.parity = (5 * k + st) & 1;
-      L.step = k;
-      L.a = dgw::kA[st];
-      L.b = dgw::kB[st];
-      L.c = dgw::kC[st];
-      e = dgw::launch_stage_batch(b->N, b->precision == DGW_PRECISION_MIXED, L, grid, cs);
-    }
-  }
-  if (e == cudaSuccess) {
-    dgw::batch_advance_kernel<<<(n + 127) / 128, 128, 0, cs>>>(b->d_solves, n, 2);
-    e = cudaGetLastError();
-  }
-  cudaGraph_t g = nullptr;
-  cudaError_t e2 = cudaStreamEndCapture(cs, &g);
-  if (e != cudaSuccess || e2 != cudaSuccess) {
-    if (g) cudaGraphDestroy(g);
-    return bfail(b, DGW_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
-  }
-  b->graph = g;
-  e = cudaGraphInstantiate(&b->exec, g, 0);
-  if (e != cudaSuccess) {
-    drop_graph(b);
-    return bfail(b, DGW_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e));
-  }
   return DGW_OK;
 }
 
@@ -240,7 +246,7 @@ dgw_status dgw_batch_run(dgw_batch* b, int npairs, void* stream) {
   if (!b) return bfail(nullptr, DGW_ERR_ARG, "null batch");
   if (npairs < 0) return bfail(b, DGW_ERR_ARG, "npairs must be >= 0");
   if (b->nsolves == 0 || npairs == 0) return DGW_OK;
-  if (!b->exec) return bfail(b, DGW_ERR_STATE, "batch not set");
+  if (!b->exec) return bfail(b, DGW_ERR_STATE, "batch has no recorded graph");
   if (cudaSetDevice(b->device) != cudaSuccess) return bfail(b, DGW_ERR_CUDA, "cudaSetDevice failed");
   for (int i = 0; i < npairs; ++i) {
     cudaError_t e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);

@@ -262,11 +262,6 @@ dgw_status dgw_create(dgw_ctx** out, int device, const dgw_config* cfg) {
     delete c;
     return fail(nullptr, DGW_ERR_CUDA, "set-up stream");
   }
-  if (cudaMallocHost((void**)&c->pinned, sizeof(double)) != cudaSuccess) {
-    cudaStreamDestroy(c->setup);
-    delete c;
-    return fail(nullptr, DGW_ERR_OOM, "pinned host slot");
-  }
   *out = c;
   return DGW_OK;
 }
@@ -275,7 +270,6 @@ dgw_status dgw_destroy(dgw_ctx* c) {
   if (!c) return DGW_OK;
   cudaSetDevice(c->device);
   free_mesh(c);
-  if (c->pinned) cudaFreeHost(c->pinned);
   if (c->setup) cudaStreamDestroy(c->setup);
   delete c;
   return DGW_OK;
@@ -560,9 +554,10 @@ dgw_status dgw_stage_energy(dgw_ctx* c, const double* u_in, double* u_out, doubl
     return st;
   double* result = c->stage_partials + c->stage_ctas;
   DGW_CUDA(c, dgw::launch_energy_final(c->stage_partials, c->stage_ctas, result, s), "energy reduction");
-  DGW_CUDA(c, cudaMemcpyAsync(c->pinned, result, sizeof(double), cudaMemcpyDeviceToHost, s), "copy energy");
+  double value = 0.0;
+  DGW_CUDA(c, cudaMemcpyAsync(&value, result, sizeof(double), cudaMemcpyDeviceToHost, s), "copy energy");
   DGW_CUDA(c, cudaStreamSynchronize(s), "stage energy");
-  *energy_out = *c->pinned;
+  *energy_out = value;
   if (!std::isfinite(*energy_out)) return fail(c, DGW_ERR_UNSTABLE, "energy is not finite");
   return DGW_OK;
 }
@@ -623,9 +618,10 @@ dgw_status dgw_energy(dgw_ctx* c, const double* u, double* energy_out, void* str
   }
   double* result = c->partials + dgw::kEnergyBlocks;
   DGW_CUDA(c, dgw::launch_energy(ud, c->wJ, c->ec, c->nel, Np_of(c->cfg.N), c->partials, result, s), "energy kernels");
-  DGW_CUDA(c, cudaMemcpyAsync(c->pinned, result, sizeof(double), cudaMemcpyDeviceToHost, s), "copy energy");
+  double value = 0.0;
+  DGW_CUDA(c, cudaMemcpyAsync(&value, result, sizeof(double), cudaMemcpyDeviceToHost, s), "copy energy");
   DGW_CUDA(c, cudaStreamSynchronize(s), "energy");
-  *energy_out = *c->pinned;
+  *energy_out = value;
   if (!std::isfinite(*energy_out)) return fail(c, DGW_ERR_UNSTABLE, "energy is not finite");
   return DGW_OK;
 }

@@ -84,11 +84,17 @@ struct BatchSolve {
   long long tile0;        // first batch tile of this solve
 };
 
+// Composition of a batch, read by the kernels from device memory so that a
+// recorded graph stays valid when solves join or leave.
+struct BatchHeader {
+  int nsolves;
+  long long total_tiles;
+};
+
 // One launch of the batched stage kernel.
 struct BatchLaunch {
   const BatchSolve* solves;
-  int nsolves;
-  long long total_tiles;
+  const BatchHeader* hdr;
   int parity;             // stage index within the replayed step pair, mod 2
   int step;               // step within the pair (0 or 1)
   double a, b, c;         // LSRK coefficients of this stage
@@ -150,7 +156,6 @@ struct dgw_ctx {
   int stage_ctas = 0;
   double* stage_u = nullptr;   // host-pointer staging buffers
   double* stage_res = nullptr;
-  double* pinned = nullptr;    // pinned host slot for the energy value
   double* src_w = nullptr;     // point-force weights [3][Np] (device)
   long long src_elem = -1;
   double src_f0 = 0.0, src_t0 = 0.0;

@@ -581,9 +581,11 @@ __global__ void __launch_bounds__(Shape<N>::NT) stage_batch_kernel(const BatchLa
   __shared__ long long local_tile;
   Real* D_s = reinterpret_cast<Real*>(smem_raw + StageSmem<N, Real>::d_off);
   for (int i = threadIdx.x; i < Shape<N>::n * Shape<N>::n; i += Shape<N>::NT) D_s[i] = static_cast<Real>(L.D[i]);
-  for (long long tile = blockIdx.x; tile < L.total_tiles; tile += gridDim.x) {
+  const long long total_tiles = L.hdr->total_tiles;
+  const int nsolves = L.hdr->nsolves;
+  for (long long tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
     if (threadIdx.x == 0) {
-      int lo = 0, hi = L.nsolves - 1;
+      int lo = 0, hi = nsolves - 1;
       while (lo < hi) {
         const int mid = (lo + hi + 1) / 2;
         if (L.solves[mid].tile0 <= tile) lo = mid; else hi = mid - 1;

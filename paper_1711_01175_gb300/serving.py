@@ -5,11 +5,12 @@ step count).  The server admits a waiting request as soon as its device
 memory fits the budget, keeps every admitted solve's fields on the device,
 and advances all admitted solves of one degree together through a
 `dgw_batch` (one persistent batched stage kernel per stage over the elements
-of every solve, replayed from a captured CUDA graph of two LSRK steps).
-Solves of different degrees run in separate batches on separate streams, so
-their work overlaps on the device.  Between graph replays the server admits
-new arrivals and retires finished solves (their composition change makes the
-batch capture a new graph).  Latency is arrival -> result on the host.
+of every solve, replayed from a CUDA graph of two LSRK steps recorded once
+per batch).  Solves of different degrees run in separate batches on separate
+streams, so their work overlaps on the device.  Between graph replays the
+server admits new arrivals and retires finished solves; a composition change
+is a stream-ordered descriptor upload.  Latency is arrival -> result on the
+host.
 
 `one_at_a_time` is the reference policy: requests are served strictly in
 arrival order, each alone with dgw_step.
@@ -63,11 +64,12 @@ class _Solve:
 class _Group:
     """The batch of one degree and its stream."""
 
-    def __init__(self, N, precision):
+    def __init__(self, N, precision, max_solves=4096):
         import torch
         self.N = N
         self.stream = torch.cuda.Stream()
-        st, self.h = capi.dgw_batch_create(torch.cuda.current_device(), N, 0 if precision == "fp64" else 1, 1)
+        st, self.h = capi.dgw_batch_create(torch.cuda.current_device(), N, 0 if precision == "fp64" else 1, 1,
+                                           max_solves)
         if st != 0:
             raise capi.DGWError(st, capi.dgw_last_error(None))
         self.solves = []
@@ -99,20 +101,45 @@ def _finish(solve, t0):
     return dict(rid=solve.req.rid, energy=e, state=u, done=time.perf_counter() - t0)
 
 
-def continuous_batching(requests, precision="mixed", memory_budget=40e9, pairs_per_tick=4, keep_states=False):
-    """Serve `requests` (sorted by arrival) with continuous batching."""
+def _nodes(req):
+    return req.E ** 3 * (req.N + 1) ** 3
+
+
+def continuous_batching(requests, precision="mixed", memory_budget=40e9, pairs_per_tick=4, keep_states=False,
+                        max_active_nodes=None):
+    """Serve `requests` (sorted by arrival) with continuous batching.
+
+    Each tick: enqueue up to `pairs_per_tick` step pairs for every non-empty
+    batch (its composition change, if any, is a stream-ordered descriptor
+    upload before them); while the GPU runs, admit arrived requests that fit
+    the memory budget (their set-up overlaps the GPU work; they join at the
+    next tick); then wait for the tick and retire finished solves.
+
+    Admission is FIFO and bounded twice: by the memory budget, and by
+    `max_active_nodes` (default: two waves of resident threads on the device)
+    so that batching fills the GPU with small solves without turning the
+    queue into processor sharing, which on a saturated device finishes every
+    request later than first-come first-served."""
     import torch
+    if max_active_nodes is None:
+        props = torch.cuda.get_device_properties(torch.cuda.current_device())
+        max_active_nodes = 2 * props.multi_processor_count * props.max_threads_per_multi_processor
     pending = deque(sorted(requests, key=lambda r: r.arrival))
     waiting = deque()
     groups = {}
     used = 0
     results = {}
     t0 = time.perf_counter()
-    while pending or waiting or any(g.solves for g in groups.values()):
+
+    def admit():
+        nonlocal used
         now = time.perf_counter() - t0
         while pending and pending[0].arrival <= now:
             waiting.append(pending.popleft())
         while waiting and used + bytes_per_request(waiting[0].E, waiting[0].N, precision) <= memory_budget:
+            active_nodes = sum(_nodes(s.req) for g in groups.values() for s in g.solves)
+            if active_nodes > 0 and active_nodes + _nodes(waiting[0]) > max_active_nodes:
+                break
             req = waiting.popleft()
             g = groups.get(req.N)
             if g is None:
@@ -121,11 +148,9 @@ def continuous_batching(requests, precision="mixed", memory_budget=40e9, pairs_p
             used += s.bytes
             g.solves.append(s)
             g.dirty = True
+
+    while pending or waiting or any(g.solves for g in groups.values()):
         active = [g for g in groups.values() if g.solves]
-        if not active:
-            if pending:
-                time.sleep(max(0.0, pending[0].arrival - (time.perf_counter() - t0)))
-            continue
         for g in active:
             if g.dirty:
                 g.reset()
@@ -137,6 +162,11 @@ def continuous_batching(requests, precision="mixed", memory_budget=40e9, pairs_p
                 s.steps_done += 2 * k
             g.event = torch.cuda.Event()
             g.event.record(g.stream)
+        admit()
+        if not active:
+            if pending and not waiting:
+                time.sleep(max(0.0, pending[0].arrival - (time.perf_counter() - t0)))
+            continue
         for g in active:
             g.event.synchronize()
             finished = [s for s in g.solves if s.steps_done >= s.req.steps]

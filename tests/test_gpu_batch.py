@@ -46,7 +46,7 @@ class Batch:
     def __init__(self, N, precision="fp64"):
         from paper_1711_01175_gb300 import capi
         self.capi = capi
-        st, self.h = capi.dgw_batch_create(0, N, 0 if precision == "fp64" else 1, 1)
+        st, self.h = capi.dgw_batch_create(0, N, 0 if precision == "fp64" else 1, 1, 64)
         assert st == 0, capi.dgw_last_error(None)
 
     def set(self, items, t0s, stream):
@@ -91,7 +91,7 @@ def test_batch_matches_single_solves_with_composition_change(precision):
     left = items[1]
     got_left = left["u"].cpu().numpy()
     cont = [items[0], items[2], late]
-    b.set(cont, [4 * items[0]["dt"], 4 * items[2]["dt"], 0.0], stream)
+    b.set(cont, [4 * items[0]["dt"], 4 * items[2]["dt"], 0.0], stream)       # no new graph: uploads only
     b.run(2, stream)
     torch.cuda.synchronize()
     assert rel_l2(got_left, alone(left, 4)) < BATCH_TOL
