@@ -194,14 +194,17 @@ dgw_status dgw_dt_cfl(dgw_ctx* ctx, double* dt_out);
 /* ---- Batches: many solves advanced together (serving) -------------------
  * A batch advances solves of one degree N, precision and flux choice, each
  * owned by its own context (mesh, medium, point force), in lock step: every
- * launch of the persistent batched stage kernel covers the elements of all
- * of them.  Not part of the paper (its runs are single solves); the
+ * launch of the batched stage kernel covers the elements of all of them (one
+ * CTA per tile).  Not part of the paper (its runs are single solves); the
  * arithmetic per element is the one of dgw_stage. */
 typedef struct dgw_batch dgw_batch;
 
+/* Most solves in one batch (their descriptors are kernel parameters). */
+#define DGW_BATCH_MAX_SOLVES 128
+
 /* Create an empty batch for degree N, precision and flux_tau on `device`,
- * holding up to max_solves solves.  Records the CUDA graph of two LSRK steps
- * once; the kernels read the batch composition from device memory. */
+ * holding up to max_solves (1..DGW_BATCH_MAX_SOLVES) solves.  Records the
+ * CUDA graph of two LSRK steps once. */
 dgw_status dgw_batch_create(dgw_batch** out, int device, int N, int precision, int flux_tau, int max_solves);
 
 /* Free the batch (not the contexts or buffers it referenced; NULL accepted). */
@@ -212,9 +215,11 @@ dgw_status dgw_batch_destroy(dgw_batch* b);
  * [9][nel_i][Np], the state in and out and the LSRK register), step size
  * dt[i] and current time t0[i] (for the point force).  The context's second
  * state buffer serves as the stage ping-pong partner, so a context belongs to
- * at most one batch at a time.  Enqueues the descriptor uploads on `stream`
- * (ordered after earlier replays on that stream; no synchronisation, no new
- * graph).  Call again whenever the set of solves changes, passing each
+ * at most one batch at a time.  Enqueues the upload of the times on `stream`
+ * and rewrites the descriptors in the batch's graph: the new composition
+ * applies to replays enqueued after this call (use the same stream for set
+ * and run), replays already enqueued keep theirs; no synchronisation, no new
+ * graph.  Call again whenever the set of solves changes, passing each
  * continuing solve's current time.  DGW_ERR_ARG beyond max_solves. */
 dgw_status dgw_batch_set(dgw_batch* b, int n, dgw_ctx* const* ctxs, double* const* u, double* const* res,
                          const double* dt, const double* t0, void* stream);

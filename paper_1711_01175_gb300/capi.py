@@ -18,6 +18,7 @@ STATUS = {0: "DGW_OK", -1: "DGW_ERR_ARG", -2: "DGW_ERR_STATE", -3: "DGW_ERR_OOM"
 DGW_PRECISION_FP64 = 0
 DGW_PRECISION_MIXED = 1
 DGW_BC_INTERIOR, DGW_BC_FREE_SURFACE, DGW_BC_ABSORBING = 0, 1, 2
+DGW_BATCH_MAX_SOLVES = 128
 
 
 class dgw_config(ctypes.Structure):
@@ -168,7 +169,7 @@ def dgw_dt_cfl(ctx):
     return st, out.value
 
 
-def dgw_batch_create(device, N, precision, flux_tau, max_solves=1024):
+def dgw_batch_create(device, N, precision, flux_tau, max_solves=DGW_BATCH_MAX_SOLVES):
     h = _P()
     st = load().dgw_batch_create(ctypes.byref(h), device, N, precision, flux_tau, max_solves)
     return st, h

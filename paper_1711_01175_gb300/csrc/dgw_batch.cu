@@ -3,13 +3,15 @@
 // A batch holds solves of one degree, precision and flux, each owned by its
 // own context (mesh, medium, source) with caller-owned state and register.
 // dgw_batch_create records a CUDA graph of two LSRK steps: ten launches of the
-// persistent batched stage kernel (every launch covers the tiles of all
-// solves; the state alternates between the caller's buffer and the context's
-// second buffer and is back in the caller's buffer after ten stages) and one
-// launch that advances each solve's device time by 2 dt.  The kernels read
-// the batch composition (descriptors, count, tile total) from device memory,
-// so dgw_batch_set only enqueues uploads on the caller's stream -- no new
-// recording, no synchronisation -- and dgw_batch_run replays the graph.
+// batched stage kernel (one CTA per tile of all solves; the state alternates
+// between the caller's buffer and the context's second buffer and is back in
+// the caller's buffer after ten stages) and one launch that advances each
+// solve's device time by 2 dt.  The solve descriptors are parameters of the
+// stage launches: dgw_batch_set rewrites them, with the grid, in the ten stage
+// nodes of the instantiated graph (an update that applies to later replays
+// only, so replays already enqueued keep their composition) and enqueues the
+// upload of the solves' times and steps on the caller's stream; no new
+// recording, no synchronisation.  dgw_batch_run replays the graph.
 #include <cmath>
 #include <string>
 #include <vector>
@@ -18,24 +20,25 @@
 
 namespace dgw {
 
-cudaError_t launch_stage_batch_fp64(int N, const BatchLaunch& L, int grid, cudaStream_t s);
-cudaError_t launch_stage_batch_mixed(int N, const BatchLaunch& L, int grid, cudaStream_t s);
-cudaError_t prepare_stage_batch_fp64(int N, int sm_count, int* grid);
-cudaError_t prepare_stage_batch_mixed(int N, int sm_count, int* grid);
+cudaError_t launch_stage_batch_fp64(int N, const BatchLaunch& L, const BatchSet& S, int grid, cudaStream_t s);
+cudaError_t launch_stage_batch_mixed(int N, const BatchLaunch& L, const BatchSet& S, int grid, cudaStream_t s);
+cudaError_t prepare_stage_batch_fp64(int N);
+cudaError_t prepare_stage_batch_mixed(int N);
 
-cudaError_t launch_stage_batch(int N, bool mixed, const BatchLaunch& L, int grid, cudaStream_t s) {
-  return mixed ? launch_stage_batch_mixed(N, L, grid, s) : launch_stage_batch_fp64(N, L, grid, s);
+cudaError_t launch_stage_batch(int N, bool mixed, const BatchLaunch& L, const BatchSet& S, int grid, cudaStream_t s) {
+  return mixed ? launch_stage_batch_mixed(N, L, S, grid, s) : launch_stage_batch_fp64(N, L, S, grid, s);
 }
 
-cudaError_t prepare_stage_batch(int N, bool mixed, int sm_count, int* grid) {
-  return mixed ? prepare_stage_batch_mixed(N, sm_count, grid) : prepare_stage_batch_fp64(N, sm_count, grid);
+cudaError_t prepare_stage_batch(int N, bool mixed) {
+  return mixed ? prepare_stage_batch_mixed(N) : prepare_stage_batch_fp64(N);
 }
 
 namespace {
 
-__global__ void batch_advance_kernel(const BatchSolve* solves, const BatchHeader* hdr, int nsteps) {
+// times[i] += nsteps dt[i] over every slot (unused slots hold dt = 0).
+__global__ void batch_advance_kernel(double* times, const double* dts, int nsteps) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < hdr->nsolves) *solves[i].t += nsteps * solves[i].dt;
+  if (i < kBatchMaxSolves) times[i] += nsteps * dts[i];
 }
 
 // LSRK(5,4) of Carpenter & Kennedy (1994), 2N-storage, five stages, fourth order.
@@ -56,16 +59,17 @@ struct dgw_batch {
   int precision = 0;
   int tau = 1;
   int sm_count = 0;
-  int grid = 0;
   int nsolves = 0;
-  long long total_tiles = 0;
-  dgw::BatchSolve* d_solves = nullptr;   // [capacity]
-  dgw::BatchHeader* d_hdr = nullptr;
-  double* d_times = nullptr;             // [capacity]
   int capacity = 0;
-  std::vector<dgw::BatchSolve> h_solves;
+  double* d_times = nullptr;             // [kBatchMaxSolves] start time of the current step pair
+  double* d_dts = nullptr;               // [kBatchMaxSolves] step sizes (0 in unused slots)
+  double h_tdt[2 * dgw::kBatchMaxSolves];   // staging of the times and steps of the last set
+  dgw::BatchSet set{};                   // composition of the last set
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  std::vector<cudaGraphNode_t> stage_nodes;   // the ten stage launches of the graph
+  std::vector<cudaKernelNodeParams> stage_params;
+  std::vector<dgw::BatchLaunch> stage_launch;   // their fixed parameters
   cudaStream_t capture = nullptr;   // private stream the graph is recorded on
   std::string err;
 };
@@ -107,7 +111,8 @@ dgw_status dgw_batch_create(dgw_batch** out, int device, int N, int precision, i
   if (precision != DGW_PRECISION_FP64 && precision != DGW_PRECISION_MIXED)
     return bfail(nullptr, DGW_ERR_ARG, "unknown precision");
   if (flux_tau != 0 && flux_tau != 1) return bfail(nullptr, DGW_ERR_ARG, "flux_tau must be 0 or 1");
-  if (max_solves < 1 || max_solves > (1 << 20)) return bfail(nullptr, DGW_ERR_ARG, "max_solves outside 1..2^20");
+  if (max_solves < 1 || max_solves > dgw::kBatchMaxSolves)
+    return bfail(nullptr, DGW_ERR_ARG, "max_solves outside 1..DGW_BATCH_MAX_SOLVES");
   if (cudaSetDevice(device) != cudaSuccess) return bfail(nullptr, DGW_ERR_CUDA, "cudaSetDevice failed");
   dgw_batch* b = new dgw_batch();
   b->device = device;
@@ -118,30 +123,25 @@ dgw_status dgw_batch_create(dgw_batch** out, int device, int N, int precision, i
   cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, device);
   auto bail = [&](dgw_status st, const std::string& msg) {
     drop_graph(b);
-    if (b->d_solves) cudaFree(b->d_solves);
-    if (b->d_hdr) cudaFree(b->d_hdr);
     if (b->d_times) cudaFree(b->d_times);
     if (b->capture) cudaStreamDestroy(b->capture);
     delete b;
     return bfail(nullptr, st, msg);
   };
-  cudaError_t e = dgw::prepare_stage_batch(N, precision == DGW_PRECISION_MIXED, b->sm_count, &b->grid);
+  cudaError_t e = dgw::prepare_stage_batch(N, precision == DGW_PRECISION_MIXED);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
   if (e != cudaSuccess) return bail(DGW_ERR_CUDA, std::string("batch kernel set-up: ") + cudaGetErrorString(e));
-  if (cudaMalloc(&b->d_solves, max_solves * sizeof(dgw::BatchSolve)) != cudaSuccess ||
-      cudaMalloc(&b->d_hdr, sizeof(dgw::BatchHeader)) != cudaSuccess ||
-      cudaMalloc(&b->d_times, max_solves * sizeof(double)) != cudaSuccess)
-    return bail(DGW_ERR_OOM, "batch descriptors");
-  dgw::BatchHeader h0{0, 0};
-  if (cudaMemcpyAsync(b->d_hdr, &h0, sizeof(h0), cudaMemcpyHostToDevice, b->capture) != cudaSuccess ||
+  if (cudaMalloc(&b->d_times, 2 * dgw::kBatchMaxSolves * sizeof(double)) != cudaSuccess)
+    return bail(DGW_ERR_OOM, "batch times");
+  b->d_dts = b->d_times + dgw::kBatchMaxSolves;
+  if (cudaMemsetAsync(b->d_times, 0, 2 * dgw::kBatchMaxSolves * sizeof(double), b->capture) != cudaSuccess ||
       cudaStreamSynchronize(b->capture) != cudaSuccess)
-    return bail(DGW_ERR_CUDA, "batch header");
-  // Record two LSRK steps once; the kernels read the composition from device memory.
+    return bail(DGW_ERR_CUDA, "batch times");
+  // Record two LSRK steps once, for an empty composition.
   int epb = 0, nt = 0;
   dgw::stage_shape(N, &epb, &nt);
   dgw::BatchLaunch L{};
-  L.solves = b->d_solves;
-  L.hdr = b->d_hdr;
+  L.times = b->d_times;
   L.tau = flux_tau ? 1.0 : 0.0;
   dgw::RefElem R;
   dgw::build_ref_elem(N, &R);
@@ -158,11 +158,11 @@ dgw_status dgw_batch_create(dgw_batch** out, int device, int N, int precision, i
       L.a = dgw::kA[st];
       L.b = dgw::kB[st];
       L.c = dgw::kC[st];
-      e = dgw::launch_stage_batch(N, precision == DGW_PRECISION_MIXED, L, b->grid, cs);
+      e = dgw::launch_stage_batch(N, precision == DGW_PRECISION_MIXED, L, b->set, 1, cs);
     }
   }
   if (e == cudaSuccess) {
-    dgw::batch_advance_kernel<<<(max_solves + 127) / 128, 128, 0, cs>>>(b->d_solves, b->d_hdr, 2);
+    dgw::batch_advance_kernel<<<(dgw::kBatchMaxSolves + 127) / 128, 128, 0, cs>>>(b->d_times, b->d_dts, 2);
     e = cudaGetLastError();
   }
   cudaGraph_t g = nullptr;
@@ -172,6 +172,25 @@ dgw_status dgw_batch_create(dgw_batch** out, int device, int N, int precision, i
     return bail(DGW_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
   }
   b->graph = g;
+  // The stage launches are the kernel nodes other than the time advance.
+  size_t nn = 0;
+  e = cudaGraphGetNodes(g, nullptr, &nn);
+  std::vector<cudaGraphNode_t> nodes(nn);
+  if (e == cudaSuccess && nn > 0) e = cudaGraphGetNodes(g, nodes.data(), &nn);
+  for (size_t i = 0; i < nn && e == cudaSuccess; ++i) {
+    cudaGraphNodeType ty;
+    e = cudaGraphNodeGetType(nodes[i], &ty);
+    if (e != cudaSuccess || ty != cudaGraphNodeTypeKernel) continue;
+    cudaKernelNodeParams kp{};
+    e = cudaGraphKernelNodeGetParams(nodes[i], &kp);
+    if (e == cudaSuccess && kp.func != reinterpret_cast<void*>(&dgw::batch_advance_kernel)) {
+      b->stage_nodes.push_back(nodes[i]);
+      b->stage_params.push_back(kp);
+      b->stage_launch.push_back(*static_cast<const dgw::BatchLaunch*>(kp.kernelParams[0]));
+    }
+  }
+  if (e == cudaSuccess && b->stage_nodes.size() != 10) e = cudaErrorUnknown;
+  if (e != cudaSuccess) return bail(DGW_ERR_CUDA, std::string("graph nodes: ") + cudaGetErrorString(e));
   e = cudaGraphInstantiate(&b->exec, g, 0);
   if (e != cudaSuccess) return bail(DGW_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e));
   *out = b;
@@ -182,8 +201,6 @@ dgw_status dgw_batch_destroy(dgw_batch* b) {
   if (!b) return DGW_OK;
   cudaSetDevice(b->device);
   drop_graph(b);
-  if (b->d_solves) cudaFree(b->d_solves);
-  if (b->d_hdr) cudaFree(b->d_hdr);
   if (b->d_times) cudaFree(b->d_times);
   if (b->capture) cudaStreamDestroy(b->capture);
   delete b;
@@ -196,7 +213,8 @@ dgw_status dgw_batch_set(dgw_batch* b, int n, dgw_ctx* const* ctxs, double* cons
   if (n < 0 || (n > 0 && (!ctxs || !u || !res || !dt || !t0))) return bfail(b, DGW_ERR_ARG, "bad arguments");
   if (cudaSetDevice(b->device) != cudaSuccess) return bfail(b, DGW_ERR_CUDA, "cudaSetDevice failed");
   cudaStream_t s = (cudaStream_t)stream;
-  std::vector<dgw::BatchSolve> hs(n);
+  if (n > b->capacity) return bfail(b, DGW_ERR_ARG, "more solves than the batch capacity");
+  dgw::BatchSet hs{};
   long long tiles = 0;
   int epb = 0, nt = 0;
   dgw::stage_shape(b->N, &epb, &nt);
@@ -208,7 +226,7 @@ dgw_status dgw_batch_set(dgw_batch* b, int n, dgw_ctx* const* ctxs, double* cons
     if (!u[i] || !res[i] || u[i] == res[i] || !device_ptr(u[i]) || !device_ptr(res[i]))
       return bfail(b, DGW_ERR_ARG, "solve " + std::to_string(i) + ": u and res must be distinct device buffers");
     if (!(dt[i] > 0.0) || !std::isfinite(t0[i])) return bfail(b, DGW_ERR_ARG, "need dt > 0 and finite t0");
-    dgw::BatchSolve& d = hs[i];
+    dgw::BatchSolve& d = hs.s[i];
     d.u[0] = u[i];
     d.u[1] = c->u2;
     d.res = res[i];
@@ -225,20 +243,31 @@ dgw_status dgw_batch_set(dgw_batch* b, int n, dgw_ctx* const* ctxs, double* cons
     d.tile0 = tiles;
     tiles += (c->nel + epb - 1) / epb;
   }
-  if (n > b->capacity) return bfail(b, DGW_ERR_ARG, "more solves than the batch capacity");
-  for (int i = 0; i < n; ++i) hs[i].t = b->d_times + i;
-  // Stream-ordered uploads: earlier replays on this stream finish first.  The
-  // host copies live in the batch until the next set (pageable sources are
-  // staged by the runtime before the call returns).
-  b->h_solves = hs;
-  dgw::BatchHeader hdr{n, tiles};
-  if ((n > 0 && cudaMemcpyAsync(b->d_solves, b->h_solves.data(), n * sizeof(dgw::BatchSolve), cudaMemcpyHostToDevice,
-                                s) != cudaSuccess) ||
-      (n > 0 && cudaMemcpyAsync(b->d_times, t0, n * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess) ||
-      cudaMemcpyAsync(b->d_hdr, &hdr, sizeof(hdr), cudaMemcpyHostToDevice, s) != cudaSuccess)
-    return bfail(b, DGW_ERR_CUDA, "upload batch descriptors");
+  if (tiles > 0x7fffffffLL) return bfail(b, DGW_ERR_ARG, "more than 2^31 - 1 tiles in the batch");
+  hs.nsolves = n;
+  hs.total_tiles = tiles;
+  // Times and steps: a stream-ordered upload (earlier replays on this stream
+  // finish first; the runtime stages the pageable source before returning).
+  for (int i = 0; i < dgw::kBatchMaxSolves; ++i) {
+    b->h_tdt[i] = i < n ? t0[i] : 0.0;
+    b->h_tdt[dgw::kBatchMaxSolves + i] = i < n ? dt[i] : 0.0;
+  }
+  if (cudaMemcpyAsync(b->d_times, b->h_tdt, sizeof(b->h_tdt), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return bfail(b, DGW_ERR_CUDA, "upload batch times");
+  // Descriptors and grid (one CTA per tile) of the stage nodes, from the next
+  // replay on; replays already enqueued keep the composition they had.
+  b->set = hs;
+  const unsigned grid = tiles > 0 ? (unsigned)tiles : 1u;
+  for (size_t k = 0; k < b->stage_nodes.size(); ++k) {
+    cudaKernelNodeParams kp = b->stage_params[k];
+    void* args[2] = {&b->stage_launch[k], &b->set};
+    kp.kernelParams = args;
+    kp.extra = nullptr;
+    kp.gridDim = dim3(grid, 1, 1);
+    cudaError_t e = cudaGraphExecKernelNodeSetParams(b->exec, b->stage_nodes[k], &kp);
+    if (e != cudaSuccess) return bfail(b, DGW_ERR_CUDA, std::string("graph update: ") + cudaGetErrorString(e));
+  }
   b->nsolves = n;
-  b->total_tiles = tiles;
   return DGW_OK;
 }
 

@@ -67,7 +67,11 @@ struct StageParams {
   double D[(kMaxN + 1) * (kMaxN + 1)];
 };
 
-// One solve of a batch (device descriptor).
+// Solves per batch.  Their descriptors travel in the stage kernel's parameters
+// (constant bank: uniform, re-loadable, no registers held across the tile).
+constexpr int kBatchMaxSolves = 128;
+
+// One solve of a batch.
 struct BatchSolve {
   double* u[2];           // state ping-pong: u[0] is the caller's state, u[1] the context's second buffer
   double* res;            // LSRK register
@@ -80,21 +84,19 @@ struct BatchSolve {
   long long src_elem;
   const double* src_w;
   double src_f0, src_t0;
-  double* t;              // device start time of the current step pair
   long long tile0;        // first batch tile of this solve
 };
 
-// Composition of a batch, read by the kernels from device memory so that a
-// recorded graph stays valid when solves join or leave.
-struct BatchHeader {
+// Composition of a batch: the solves in tile order.
+struct BatchSet {
   int nsolves;
   long long total_tiles;
+  BatchSolve s[kBatchMaxSolves];
 };
 
-// One launch of the batched stage kernel.
+// One launch of the batched stage kernel (fixed when the graph is recorded).
 struct BatchLaunch {
-  const BatchSolve* solves;
-  const BatchHeader* hdr;
+  const double* times;    // [kBatchMaxSolves] device start time of the current step pair
   int parity;             // stage index within the replayed step pair, mod 2
   int step;               // step within the pair (0 or 1)
   double a, b, c;         // LSRK coefficients of this stage
@@ -105,8 +107,8 @@ struct BatchLaunch {
 };
 
 // Launchers implemented in dgw_stage_fp64.cu / dgw_stage_mixed.cu.
-cudaError_t launch_stage_batch(int N, bool mixed, const BatchLaunch& L, int grid, cudaStream_t s);
-cudaError_t prepare_stage_batch(int N, bool mixed, int sm_count, int* grid);
+cudaError_t launch_stage_batch(int N, bool mixed, const BatchLaunch& L, const BatchSet& S, int grid, cudaStream_t s);
+cudaError_t prepare_stage_batch(int N, bool mixed);
 cudaError_t launch_stage_fp64(int N, bool lsrk, const StageParams& p, cudaStream_t s);
 cudaError_t launch_stage_mixed(int N, bool lsrk, const StageParams& p, cudaStream_t s);
 cudaError_t launch_stage_adjoint(int N, int mode, const StageParams& p, cudaStream_t s);   // mode 2: ADJ, 3: GRAD

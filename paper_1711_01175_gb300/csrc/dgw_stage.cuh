@@ -569,86 +569,79 @@ __device__ __forceinline__ double ricker_dev(double t, double f0, double t0) {
   return (1.0 - 2.0 * a * a) * exp(-a * a);
 }
 
-// Persistent batched stage: CTAs walk the tiles of every solve of the batch
-// (solves of one degree and precision, each with its own mesh, medium, state
-// and source).  Thread 0 builds the solve's stage parameters in shared memory;
-// the stage time of the source is t + (step + c_s) dt with t read from device
-// memory, so the launches can be replayed from a CUDA graph.
+// Batched stage: one CTA per tile of the concatenated tile ranges of every
+// solve of the batch (solves of one degree and precision, each with its own
+// mesh, medium, state and source).  The descriptors are kernel parameters:
+// each thread finds its tile's solve by a binary search over their first
+// tiles and reads the solve's parameters from the constant bank, as the
+// single-solve kernel does.  The stage time of the source is
+// t + (step + c_s) dt with t read from device memory, so the launches can be
+// replayed from a CUDA graph; CTAs past the tile total exit.
 template <int N, typename Real>
-__global__ void __launch_bounds__(Shape<N>::NT) stage_batch_kernel(const BatchLaunch L) {
+__global__ void __launch_bounds__(Shape<N>::NT) stage_batch_kernel(const BatchLaunch L, const BatchSet S) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ StageParams ps;
-  __shared__ long long local_tile;
+  const long long tile = blockIdx.x;
+  if (tile >= S.total_tiles) return;
   Real* D_s = reinterpret_cast<Real*>(smem_raw + StageSmem<N, Real>::d_off);
   for (int i = threadIdx.x; i < Shape<N>::n * Shape<N>::n; i += Shape<N>::NT) D_s[i] = static_cast<Real>(L.D[i]);
-  const long long total_tiles = L.hdr->total_tiles;
-  const int nsolves = L.hdr->nsolves;
-  for (long long tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
-    if (threadIdx.x == 0) {
-      int lo = 0, hi = nsolves - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) / 2;
-        if (L.solves[mid].tile0 <= tile) lo = mid; else hi = mid - 1;
-      }
-      const BatchSolve& b = L.solves[lo];
-      ps.u_in = b.u[L.parity];
-      ps.out = b.u[L.parity ^ 1];
-      ps.res = b.res;
-      ps.geo = b.geo;
-      ps.fz = b.fz;
-      ps.vmapP = b.vmapP;
-      ps.mat = b.mat;
-      ps.nel = b.nel;
-      ps.a = L.a;
-      ps.b = L.b;
-      ps.dt = b.dt;
-      ps.tau = L.tau;
-      ps.w_end_inv = L.w_end_inv;
-      ps.energy_partials = nullptr;
-      ps.wJ = nullptr;
-      ps.ec = nullptr;
-      ps.pf_elems = L.pf_elems;
-      ps.src_elem = b.src_elem;
-      ps.src_w = b.src_w;
-      ps.src_amp = b.src_elem >= 0 ? ricker_dev(*b.t + (L.step + L.c) * b.dt, b.src_f0, b.src_t0) : 0.0;
-      local_tile = tile - b.tile0;
-    }
-    __syncthreads();
-    stage_tile<N, Real, kModeLsrk>(ps, local_tile, smem_raw);
-    __syncthreads();
+  int lo = 0, hi = S.nsolves - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (S.s[mid].tile0 <= tile) lo = mid; else hi = mid - 1;
   }
+  const BatchSolve& b = S.s[lo];
+  StageParams ps;
+  ps.u_in = b.u[L.parity];
+  ps.out = b.u[L.parity ^ 1];
+  ps.res = b.res;
+  ps.geo = b.geo;
+  ps.fz = b.fz;
+  ps.vmapP = b.vmapP;
+  ps.mat = b.mat;
+  ps.nel = b.nel;
+  ps.a = L.a;
+  ps.b = L.b;
+  ps.dt = b.dt;
+  ps.tau = L.tau;
+  ps.w_end_inv = L.w_end_inv;
+  ps.energy_partials = nullptr;
+  ps.wJ = nullptr;
+  ps.ec = nullptr;
+  ps.pf_elems = L.pf_elems;
+  ps.grad_el = nullptr;
+  ps.grad_face = nullptr;
+  ps.src_elem = b.src_elem;
+  ps.src_w = b.src_w;
+  ps.src_amp = 0.0;
+  if (b.src_elem >= 0 && b.src_elem / Shape<N>::EPB == tile - b.tile0)
+    ps.src_amp = ricker_dev(L.times[lo] + (L.step + L.c) * b.dt, b.src_f0, b.src_t0);
+  stage_tile<N, Real, kModeLsrk>(ps, tile - b.tile0, smem_raw);
 }
 
 template <int N, typename Real>
-cudaError_t launch_stage_batch_t(const BatchLaunch& L, int grid, cudaStream_t s) {
+cudaError_t launch_stage_batch_t(const BatchLaunch& L, const BatchSet& S, int grid, cudaStream_t s) {
   const size_t smem = StageSmem<N, Real>::bytes;
-  stage_batch_kernel<N, Real><<<grid, Shape<N>::NT, smem, s>>>(L);
+  stage_batch_kernel<N, Real><<<grid, Shape<N>::NT, smem, s>>>(L, S);
   return cudaGetLastError();
 }
 
-// Set the kernel attributes and return the persistent grid (resident CTAs).
+// Set the kernel attributes of the batched stage kernel.
 template <int N, typename Real>
-cudaError_t prepare_stage_batch_t(int sm_count, int* grid) {
+cudaError_t prepare_stage_batch_t() {
   const size_t smem = StageSmem<N, Real>::bytes;
   cudaError_t err = cudaFuncSetAttribute(stage_batch_kernel<N, Real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
   if (err != cudaSuccess) return err;
-  err = cudaFuncSetAttribute(stage_batch_kernel<N, Real>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             (int)cudaSharedmemCarveoutMaxShared);
-  if (err != cudaSuccess) return err;
-  int per_sm = 0;
-  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_batch_kernel<N, Real>, Shape<N>::NT, smem);
-  if (err != cudaSuccess) return err;
-  *grid = (per_sm > 0 ? per_sm : 1) * sm_count;
-  return cudaSuccess;
+  return cudaFuncSetAttribute(stage_batch_kernel<N, Real>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                              (int)cudaSharedmemCarveoutMaxShared);
 }
 
 template <typename Real>
-cudaError_t launch_stage_batch_any(int N, const BatchLaunch& L, int grid, cudaStream_t s) {
+cudaError_t launch_stage_batch_any(int N, const BatchLaunch& L, const BatchSet& S, int grid, cudaStream_t s) {
   switch (N) {
 #define DGW_BCASE(NN) \
   case NN:            \
-    return launch_stage_batch_t<NN, Real>(L, grid, s);
+    return launch_stage_batch_t<NN, Real>(L, S, grid, s);
     DGW_BCASE(1) DGW_BCASE(2) DGW_BCASE(3) DGW_BCASE(4) DGW_BCASE(5) DGW_BCASE(6) DGW_BCASE(7)
 #undef DGW_BCASE
     default:
@@ -657,11 +650,11 @@ cudaError_t launch_stage_batch_any(int N, const BatchLaunch& L, int grid, cudaSt
 }
 
 template <typename Real>
-cudaError_t prepare_stage_batch_any(int N, int sm_count, int* grid) {
+cudaError_t prepare_stage_batch_any(int N) {
   switch (N) {
 #define DGW_PCASE(NN) \
   case NN:            \
-    return prepare_stage_batch_t<NN, Real>(sm_count, grid);
+    return prepare_stage_batch_t<NN, Real>();
     DGW_PCASE(1) DGW_PCASE(2) DGW_PCASE(3) DGW_PCASE(4) DGW_PCASE(5) DGW_PCASE(6) DGW_PCASE(7)
 #undef DGW_PCASE
     default:

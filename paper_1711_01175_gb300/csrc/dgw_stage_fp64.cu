@@ -26,12 +26,12 @@ cudaError_t launch_stage_adjoint(int N, int mode, const StageParams& p, cudaStre
   return launch_stage_adjoint_any(N, mode, p, s);
 }
 
-cudaError_t launch_stage_batch_fp64(int N, const BatchLaunch& L, int grid, cudaStream_t s) {
-  return launch_stage_batch_any<double>(N, L, grid, s);
+cudaError_t launch_stage_batch_fp64(int N, const BatchLaunch& L, const BatchSet& S, int grid, cudaStream_t s) {
+  return launch_stage_batch_any<double>(N, L, S, grid, s);
 }
 
-cudaError_t prepare_stage_batch_fp64(int N, int sm_count, int* grid) {
-  return prepare_stage_batch_any<double>(N, sm_count, grid);
+cudaError_t prepare_stage_batch_fp64(int N) {
+  return prepare_stage_batch_any<double>(N);
 }
 
 }  // namespace dgw

@@ -8,12 +8,12 @@ cudaError_t launch_stage_mixed(int N, bool lsrk, const StageParams& p, cudaStrea
   return launch_stage_any<float>(N, lsrk, p, s);
 }
 
-cudaError_t launch_stage_batch_mixed(int N, const BatchLaunch& L, int grid, cudaStream_t s) {
-  return launch_stage_batch_any<float>(N, L, grid, s);
+cudaError_t launch_stage_batch_mixed(int N, const BatchLaunch& L, const BatchSet& S, int grid, cudaStream_t s) {
+  return launch_stage_batch_any<float>(N, L, S, grid, s);
 }
 
-cudaError_t prepare_stage_batch_mixed(int N, int sm_count, int* grid) {
-  return prepare_stage_batch_any<float>(N, sm_count, grid);
+cudaError_t prepare_stage_batch_mixed(int N) {
+  return prepare_stage_batch_any<float>(N);
 }
 
 }  // namespace dgw

@@ -64,7 +64,7 @@ class _Solve:
 class _Group:
     """The batch of one degree and its stream."""
 
-    def __init__(self, N, precision, max_solves=4096):
+    def __init__(self, N, precision, max_solves=capi.DGW_BATCH_MAX_SOLVES):
         import torch
         self.N = N
         self.stream = torch.cuda.Stream()
@@ -72,6 +72,7 @@ class _Group:
                                            max_solves)
         if st != 0:
             raise capi.DGWError(st, capi.dgw_last_error(None))
+        self.capacity = max_solves
         self.solves = []
         self.dirty = False
         self.event = None
@@ -115,7 +116,8 @@ def continuous_batching(requests, precision="mixed", memory_budget=40e9, pairs_p
     the memory budget (their set-up overlaps the GPU work; they join at the
     next tick); then wait for the tick and retire finished solves.
 
-    Admission is FIFO and bounded twice: by the memory budget, and by
+    Admission is FIFO and bounded three times: by a batch's capacity
+    (DGW_BATCH_MAX_SOLVES solves of one degree), by the memory budget, and by
     `max_active_nodes` (default: two waves of resident threads on the device)
     so that batching fills the GPU with small solves without turning the
     queue into processor sharing, which on a saturated device finishes every
@@ -140,8 +142,10 @@ def continuous_batching(requests, precision="mixed", memory_budget=40e9, pairs_p
             active_nodes = sum(_nodes(s.req) for g in groups.values() for s in g.solves)
             if active_nodes > 0 and active_nodes + _nodes(waiting[0]) > max_active_nodes:
                 break
+            g = groups.get(waiting[0].N)
+            if g is not None and len(g.solves) >= g.capacity:
+                break
             req = waiting.popleft()
-            g = groups.get(req.N)
             if g is None:
                 g = groups[req.N] = _Group(req.N, precision)
             s = _Solve(req, precision, g.stream)
