@@ -53,7 +53,7 @@ class _Solve:
         with torch.cuda.stream(stream):
             self.u = torch.zeros((9, m.nel, (req.N + 1) ** 3), dtype=torch.float64, device="cuda")
             self.res = torch.zeros_like(self.u)
-        self.steps_done = 0
+        self.steps_done = 0         # steps enqueued so far
         self.bytes = bytes_per_request(req.E, req.N, precision)
 
     def close(self):
@@ -62,7 +62,7 @@ class _Solve:
 
 
 class _Group:
-    """The batch of one degree and its stream."""
+    """The batch of one degree, its stream and its ticks in flight."""
 
     def __init__(self, N, precision, max_solves=capi.DGW_BATCH_MAX_SOLVES):
         import torch
@@ -73,9 +73,9 @@ class _Group:
         if st != 0:
             raise capi.DGWError(st, capi.dgw_last_error(None))
         self.capacity = max_solves
-        self.solves = []
+        self.solves = []            # the batch's composition for the next tick
         self.dirty = False
-        self.event = None
+        self.inflight = deque()     # (sequence number, event, solves that end with this tick)
 
     def reset(self):
         n = len(self.solves)
@@ -107,84 +107,120 @@ def _nodes(req):
 
 
 def continuous_batching(requests, precision="mixed", memory_budget=40e9, pairs_per_tick=4, keep_states=False,
-                        max_active_nodes=None):
+                        max_active_nodes=None, ticks_in_flight=2):
     """Serve `requests` (sorted by arrival) with continuous batching.
 
-    Each tick: enqueue up to `pairs_per_tick` step pairs for every non-empty
-    batch (its composition change, if any, is a stream-ordered descriptor
-    upload before them); while the GPU runs, admit arrived requests that fit
-    the memory budget (their set-up overlaps the GPU work; they join at the
-    next tick); then wait for the tick and retire finished solves.
+    The loop keeps up to `ticks_in_flight` ticks enqueued per batch, so the
+    device never waits for the host: a tick is up to `pairs_per_tick` step
+    pairs of the batch's current composition.  The host knows in advance how
+    many steps each solve has been given, so a solve whose last step is in a
+    tick leaves the composition of the next one before that tick has run; its
+    result is read (on a separate stream) once its tick's event has
+    completed.  Between ticks the loop admits arrived requests (their set-up
+    overlaps the device work; they join at their batch's next tick).
 
     Admission is FIFO and bounded three times: by a batch's capacity
     (DGW_BATCH_MAX_SOLVES solves of one degree), by the memory budget, and by
     `max_active_nodes` (default: two waves of resident threads on the device)
     so that batching fills the GPU with small solves without turning the
     queue into processor sharing, which on a saturated device finishes every
-    request later than first-come first-served."""
+    request later than first-come first-served.
+
+    Finished solves release their device memory when no tick is in flight
+    (freeing device memory waits for the whole device) or when admission is
+    short of memory."""
     import torch
     if max_active_nodes is None:
         props = torch.cuda.get_device_properties(torch.cuda.current_device())
         max_active_nodes = 2 * props.multi_processor_count * props.max_threads_per_multi_processor
+    for r in requests:
+        if bytes_per_request(r.E, r.N, precision) > memory_budget:
+            raise ValueError(f"request {r.rid} needs more device memory than the budget")
     pending = deque(sorted(requests, key=lambda r: r.arrival))
     waiting = deque()
     groups = {}
-    used = 0
+    used = 0                # bytes of admitted solves, including retired ones not yet released
+    active_nodes = 0        # nodes of solves not yet retired
+    retired = []
     results = {}
+    readout = torch.cuda.Stream()
+    seq = 0
     t0 = time.perf_counter()
 
-    def admit():
+    def release():
         nonlocal used
+        for s in retired:
+            used -= s.bytes
+            s.close()
+        retired.clear()
+
+    def admit():
+        nonlocal used, active_nodes
         now = time.perf_counter() - t0
         while pending and pending[0].arrival <= now:
             waiting.append(pending.popleft())
-        while waiting and used + bytes_per_request(waiting[0].E, waiting[0].N, precision) <= memory_budget:
-            active_nodes = sum(_nodes(s.req) for g in groups.values() for s in g.solves)
-            if active_nodes > 0 and active_nodes + _nodes(waiting[0]) > max_active_nodes:
+        while waiting:
+            req = waiting[0]
+            need = bytes_per_request(req.E, req.N, precision)
+            if used + need > memory_budget:
+                if not retired:
+                    break
+                release()
+                continue
+            if active_nodes > 0 and active_nodes + _nodes(req) > max_active_nodes:
                 break
-            g = groups.get(waiting[0].N)
+            g = groups.get(req.N)
             if g is not None and len(g.solves) >= g.capacity:
                 break
-            req = waiting.popleft()
+            waiting.popleft()
             if g is None:
                 g = groups[req.N] = _Group(req.N, precision)
             s = _Solve(req, precision, g.stream)
             used += s.bytes
+            active_nodes += _nodes(req)
             g.solves.append(s)
             g.dirty = True
 
-    while pending or waiting or any(g.solves for g in groups.values()):
-        active = [g for g in groups.values() if g.solves]
-        for g in active:
-            if g.dirty:
-                g.reset()
-            k = min(pairs_per_tick, min((s.req.steps - s.steps_done) // 2 for s in g.solves))
-            st = capi.dgw_batch_run(g.h, k, ctypes.c_void_p(g.stream.cuda_stream))
-            if st != 0:
-                raise capi.DGWError(st, capi.dgw_batch_last_error(g.h))
-            for s in g.solves:
-                s.steps_done += 2 * k
-            g.event = torch.cuda.Event()
-            g.event.record(g.stream)
+    while pending or waiting or any(g.solves or g.inflight for g in groups.values()):
         admit()
-        if not active:
+        for g in groups.values():
+            while g.solves and len(g.inflight) < ticks_in_flight:
+                if g.dirty:
+                    g.reset()
+                k = min(pairs_per_tick, min((s.req.steps - s.steps_done) // 2 for s in g.solves))
+                st = capi.dgw_batch_run(g.h, k, ctypes.c_void_p(g.stream.cuda_stream))
+                if st != 0:
+                    raise capi.DGWError(st, capi.dgw_batch_last_error(g.h))
+                for s in g.solves:
+                    s.steps_done += 2 * k
+                ending = [s for s in g.solves if s.steps_done >= s.req.steps]
+                if ending:
+                    g.solves = [s for s in g.solves if s.steps_done < s.req.steps]
+                    g.dirty = True
+                ev = torch.cuda.Event()
+                ev.record(g.stream)
+                g.inflight.append((seq, ev, ending))
+                seq += 1
+        busy = [g for g in groups.values() if g.inflight]
+        if not busy:
+            release()
             if pending and not waiting:
                 time.sleep(max(0.0, pending[0].arrival - (time.perf_counter() - t0)))
             continue
-        for g in active:
-            g.event.synchronize()
-            finished = [s for s in g.solves if s.steps_done >= s.req.steps]
-            if finished:
-                g.solves = [s for s in g.solves if s.steps_done < s.req.steps]
-                g.dirty = True
-                for s in finished:
+        g = min(busy, key=lambda gg: gg.inflight[0][0])
+        _, ev, ending = g.inflight.popleft()
+        ev.synchronize()
+        if ending:
+            with torch.cuda.stream(readout):
+                for s in ending:
                     r = _finish(s, t0)
                     r["latency"] = r["done"] - s.req.arrival
                     if not keep_states:
                         r.pop("state")
                     results[s.req.rid] = r
-                    used -= s.bytes
-                    s.close()
+                    active_nodes -= _nodes(s.req)
+                    retired.append(s)
+    release()
     for g in groups.values():
         g.close()
     return results, time.perf_counter() - t0

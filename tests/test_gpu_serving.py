@@ -31,11 +31,14 @@ def _requests():
     return reqs
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-6)])
-def test_each_result_same_alone_and_in_the_mix(precision, tol):
+@pytest.mark.parametrize("precision,tol,ticks", [("fp64", 1e-12, 1), ("fp64", 1e-12, 3), ("mixed", 1e-6, 2)])
+def test_each_result_same_alone_and_in_the_mix(precision, tol, ticks):
+    """`ticks` step-pair ticks in flight: composition changes are enqueued
+    while earlier ticks with another composition still run."""
     from paper_1711_01175_gb300 import serving
     reqs = _requests()
-    mixed, wall = serving.continuous_batching(reqs, precision=precision, keep_states=True, pairs_per_tick=2)
+    mixed, wall = serving.continuous_batching(reqs, precision=precision, keep_states=True, pairs_per_tick=1 if ticks > 2 else 2,
+                                              ticks_in_flight=ticks)
     alone, _ = serving.one_at_a_time(reqs, precision=precision, keep_states=True)
     assert sorted(mixed) == sorted(alone) == [r.rid for r in reqs]
     for rid in mixed:
