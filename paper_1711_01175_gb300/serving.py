@@ -1,16 +1,15 @@
 """Serving loop: continuous batching of independent wave solves on one GPU.
 
 Requests arrive over time (each its own mesh, degree, medium, point force and
-step count).  The server admits a waiting request as soon as its device
-memory fits the budget, keeps every admitted solve's fields on the device,
-and advances all admitted solves of one degree together through a
-`dgw_batch` (one persistent batched stage kernel per stage over the elements
-of every solve, replayed from a CUDA graph of two LSRK steps recorded once
-per batch).  Solves of different degrees run in separate batches on separate
-streams, so their work overlaps on the device.  Between graph replays the
-server admits new arrivals and retires finished solves; a composition change
-is a stream-ordered descriptor upload.  Latency is arrival -> result on the
-host.
+step count).  The server admits a waiting request as soon as it fits the
+memory budget and the occupancy bound, keeps every admitted solve's fields on
+the device, and advances all admitted solves of one degree together through a
+`dgw_batch` (one batched stage launch per stage over the elements of every
+solve, replayed from a CUDA graph of two LSRK steps recorded once per batch).
+Solves of different degrees run in separate batches on separate streams, so
+their work overlaps on the device.  A composition change rewrites the graph's
+descriptors for later replays while earlier ticks still run.  Latency is
+arrival -> result on the host.
 
 `one_at_a_time` is the reference policy: requests are served strictly in
 arrival order, each alone with dgw_step.
