@@ -363,6 +363,51 @@ def run_serving(args):
             "p99_ms": b["p99_ms"], "p50_ms": b["p50_ms"]}
 
 
+def run_adjoint(args):
+    """Gradient of a receiver misfit w.r.t. the per-element medium by the
+    hand-written adjoint (FP64): forward with checkpoints, then the backward
+    sweep; reports the time of each and their ratio."""
+    import torch
+    from paper_1711_01175_gb300 import Solver, reference_nodes
+    from paper_1711_01175_gb300.adjoint import receiver_traces
+    E, N, nsteps, nrec, every = args.adj_E, 4, args.adj_steps, args.adj_receivers, args.adj_checkpoint
+    mesh = wl.structured_hex_mesh(E, (True, True, False), {4: wl.BC_ABSORBING, 5: wl.BC_FREE_SURFACE}, "morton")
+    r, _ = reference_nodes(N)
+    x = wl.warped_node_coords(mesh, r, 0.1)
+    rho, lam, mu = wl.smooth_random_material(mesh, 5)
+    s = Solver(N)
+    s.upload_mesh(x, mesh.etoe, mesh.etof, mesh.orient, mesh.bc)
+    s.upload_material(rho, lam, mu)
+    centre = int(np.nonzero(np.all(mesh.cell == E // 2, axis=1))[0][0])
+    f0 = 5.0 * float(np.mean(np.sqrt(mu / rho)))
+    s.set_point_force(centre, [0.1, -0.2, 0.3], [0.0, 0.0, 1.0], f0, 0.5 / f0)
+    rng = np.random.default_rng(9)
+    top = np.nonzero(mesh.cell[:, 2] == E - 1)[0]
+    s.set_receivers(rng.choice(top, nrec, replace=False), rng.uniform(-1, 1, (nrec, 3)) * [1, 1, 0] + [0, 0, 1])
+    dt = s.dt_cfl()
+    u0 = torch.zeros((9, mesh.nel, (N + 1) ** 3), dtype=torch.float64, device="cuda")
+    data = torch.from_numpy(1e-4 * rng.standard_normal((nsteps, nrec, 3))).cuda()
+    m = torch.tensor(np.stack([rho, lam, mu]), requires_grad=True)
+    # warm-up: two steps forward and back (first launches, workspace allocation)
+    w = receiver_traces(m, s, u0, dt, 2, checkpoint_every=every)
+    torch.sum(w * w).backward()
+    m.grad = None
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tr = receiver_traces(m, s, u0, dt, nsteps, checkpoint_every=every)
+    J = 0.5 * dt * torch.sum((tr - data) ** 2)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    J.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    g = m.grad.numpy()
+    s.close()
+    return {"mesh": f"{E}^3", "N": N, "steps": nsteps, "receivers": nrec, "checkpoint_every": every,
+            "forward_s": t1 - t0, "backward_s": t2 - t1, "backward_over_forward": (t2 - t1) / (t1 - t0),
+            "gradient_norm": float(np.linalg.norm(g)), "precision": "fp64"}
+
+
 def build_workload_oracle(name, E=None):
     import oracle
     cfg = workload_config(name, E)
@@ -385,6 +430,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=256, help="elements per reference-arm step")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adj-E", type=int, default=16, help="adjoint mesh edge (the full recipe: 32)")
+    ap.add_argument("--adj-steps", type=int, default=40, help="(the full recipe: 500)")
+    ap.add_argument("--adj-receivers", type=int, default=8, help="(the full recipe: 32)")
+    ap.add_argument("--adj-checkpoint", type=int, default=10, help="(the full recipe: 50)")
     ap.add_argument("--serve-requests", type=int, default=48,
                     help="requests of the served-latency run (the full recipe: 2000)")
     ap.add_argument("--serve-rate", type=float, default=80.0, help="Poisson arrival rate per second")
@@ -486,6 +536,8 @@ def main():
         line["cpu_baseline"] = cpu_oracle_sample(cfg, data)
     if world == 1 and not args.no_serving:
         line["serving"] = run_serving(args)
+    if world == 1 and not args.no_adjoint:
+        line["adjoint"] = run_adjoint(args)
     if len(results) > 1:
         m = results["mixed"]
         line["variants"] = {"mixed": {"value": m["value"], "dtype": "f32/f64", "steps": m["steps"],
