@@ -131,13 +131,28 @@ struct StageSmem {
   static constexpr bool kPrefetchRes = std::is_same<Real, float>::value;
   static constexpr size_t u_off = 0;                                    // Real [NTILE][PK] state
   static constexpr size_t f_off = u_off + sizeof(Real) * S::NTILE * PK;  // Real [NTILE][PK] flux / face fluxes
-  static constexpr size_t fbytes = sizeof(Real) * (S::NTILE * PK > 9 * S::NFACE_ITEMS ? S::NTILE * PK : 9 * S::NFACE_ITEMS);
+  // FP64 stages A(Ja^i)u in this region before the face fluxes reuse it; FP32
+  // recomputes A(Ja^i)u at the contraction nodes and keeps only the face fluxes.
+  static constexpr size_t fwords = (kPrefetchRes || S::NTILE * PK < 9 * S::NFACE_ITEMS) ? 9 * S::NFACE_ITEMS : S::NTILE * PK;
+  static constexpr size_t fbytes = sizeof(Real) * fwords;
   static constexpr size_t g_off = f_off + ((fbytes + 15) / 16) * 16;     // Real [NTILE][PK] Ja, 1/J
   static constexpr size_t d_off = g_off + sizeof(Real) * S::NTILE * PK;  // Real [n*n]
   static constexpr size_t e_off = ((d_off + sizeof(Real) * S::n * S::n + 15) / 16) * 16;  // double [32] reduction
   static constexpr size_t r_off = e_off + sizeof(double) * 32;                            // double [9][NTILE]
   static constexpr size_t bytes = r_off + (kPrefetchRes ? sizeof(double) * 9 * S::NTILE : 0);
 };
+
+// Slots of the metric terms in a node's geometry tile: Ja^dir_k and 1/J.  FP32
+// keeps each direction in its own 16-byte group (one vector load), with 1/J in
+// the first group's spare slot; FP64 packs them (10 of 10 slots).
+template <typename Real>
+__host__ __device__ constexpr int gslot(int dir, int k) {
+  return std::is_same<Real, float>::value ? 4 * dir + k : 3 * dir + k;
+}
+template <typename Real>
+__host__ __device__ constexpr int gslot_ij() {
+  return std::is_same<Real, float>::value ? 3 : 9;
+}
 
 // Kernel modes.  RHS: write L(u).  LSRK: fused 2N-storage stage update.
 // ADJ: the reversed operator (A_k -> -A_k, same stabilisation) without Q^{-1}
@@ -222,7 +237,14 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
     }
     w[9] = 0;
     V::store10(u_s + t * PK, w);
-    V::store10(g_s + t * PK, gj);
+    if constexpr (std::is_same<Real, float>::value) {
+      float4* gp = reinterpret_cast<float4*>(g_s + t * PK);
+      gp[0] = make_float4(gj[0], gj[1], gj[2], gj[9]);
+      gp[1] = make_float4(gj[3], gj[4], gj[5], 0.f);
+      gp[2] = make_float4(gj[6], gj[7], gj[8], 0.f);
+    } else {
+      V::store10(g_s + t * PK, gj);
+    }
   }
   __syncthreads();
 
@@ -234,55 +256,90 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
 #pragma unroll
   for (int q = 0; q < 9; ++q) acc[q] = 0;
 
-#pragma unroll
-  for (int dir = 0; dir < 3; ++dir) {
-    Real m1 = 0, m2 = 0, m3 = 0;
+  if constexpr (std::is_same<Real, float>::value) {
+    // FP32: A_+(Ja^i) u at each contraction node is recomputed from the state
+    // and metric tiles (no staging, no barrier between directions).
     if (in_tile) {
-      m1 = g_s[t * PK + 3 * dir + 0];
-      m2 = g_s[t * PK + 3 * dir + 1];
-      m3 = g_s[t * PK + 3 * dir + 2];
-      Real w[10], F[10];
-      V::load9(u_s + t * PK, w);
-      apply_Apos(m1, m2, m3, w, F);
-      F[9] = 0;
-      V::store10(f_s + t * PK, F);
+#pragma unroll
+      for (int dir = 0; dir < 3; ++dir) {
+        const int stride = dir == 0 ? 1 : (dir == 1 ? n : nf);
+        const int a = dir == 0 ? ix : (dir == 1 ? iy : iz);
+        const int base = t - a * stride;
+        Real ds[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) ds[q] = 0;
+#pragma unroll
+        for (int b = 0; b < n; ++b) {
+          const Real Dab = D_s[a * n + b];
+          const int nb = base + b * stride;
+          Real w[10], F[9];
+          V::load9(u_s + nb * PK, w);
+          const float4 mb = reinterpret_cast<const float4*>(g_s + nb * PK)[dir];
+          apply_Apos(mb.x, mb.y, mb.z, w, F);
+#pragma unroll
+          for (int q = 0; q < 9; ++q) {
+            acc[q] += Dab * F[q];
+            ds[q] += Dab * w[q];
+          }
+        }
+        const float4 mt = reinterpret_cast<const float4*>(g_s + t * PK)[dir];
+        Real G[9];
+        apply_Apos(mt.x, mt.y, mt.z, ds, G);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) acc[q] += G[q];
+      }
     }
-    __syncthreads();
-    if (in_tile) {
-      const int stride = dir == 0 ? 1 : (dir == 1 ? n : nf);
-      const int a = dir == 0 ? ix : (dir == 1 ? iy : iz);
-      const int base = t - a * stride;
-      Real Drow[n];
+  } else {
 #pragma unroll
-      for (int b = 0; b < n; ++b) Drow[b] = D_s[a * n + b];
-      Real cs[9], ds[9];
-#pragma unroll
-      for (int q = 0; q < 9; ++q) cs[q] = 0;
-#pragma unroll
-      for (int b = 0; b < n; ++b) {
-        Real F[10];
-        V::load9(f_s + (base + b * stride) * PK, F);
-#pragma unroll
-        for (int q = 0; q < 9; ++q) cs[q] += Drow[b] * F[q];
+    for (int dir = 0; dir < 3; ++dir) {
+      Real m1 = 0, m2 = 0, m3 = 0;
+      if (in_tile) {
+        m1 = g_s[t * PK + 3 * dir + 0];
+        m2 = g_s[t * PK + 3 * dir + 1];
+        m3 = g_s[t * PK + 3 * dir + 2];
+        Real w[10], F[10];
+        V::load9(u_s + t * PK, w);
+        apply_Apos(m1, m2, m3, w, F);
+        F[9] = 0;
+        V::store10(f_s + t * PK, F);
       }
-#pragma unroll
-      for (int q = 0; q < 9; ++q) {
-        acc[q] += cs[q];
-        ds[q] = 0;
+      __syncthreads();
+      if (in_tile) {
+        const int stride = dir == 0 ? 1 : (dir == 1 ? n : nf);
+        const int a = dir == 0 ? ix : (dir == 1 ? iy : iz);
+        const int base = t - a * stride;
+        Real Drow[n];
+  #pragma unroll
+        for (int b = 0; b < n; ++b) Drow[b] = D_s[a * n + b];
+        Real cs[9], ds[9];
+  #pragma unroll
+        for (int q = 0; q < 9; ++q) cs[q] = 0;
+  #pragma unroll
+        for (int b = 0; b < n; ++b) {
+          Real F[10];
+          V::load9(f_s + (base + b * stride) * PK, F);
+  #pragma unroll
+          for (int q = 0; q < 9; ++q) cs[q] += Drow[b] * F[q];
+        }
+  #pragma unroll
+        for (int q = 0; q < 9; ++q) {
+          acc[q] += cs[q];
+          ds[q] = 0;
+        }
+  #pragma unroll
+        for (int b = 0; b < n; ++b) {
+          Real w[10];
+          V::load9(u_s + (base + b * stride) * PK, w);
+  #pragma unroll
+          for (int q = 0; q < 9; ++q) ds[q] += Drow[b] * w[q];
+        }
+        Real G[9];
+        apply_Apos(m1, m2, m3, ds, G);
+  #pragma unroll
+        for (int q = 0; q < 9; ++q) acc[q] += G[q];
       }
-#pragma unroll
-      for (int b = 0; b < n; ++b) {
-        Real w[10];
-        V::load9(u_s + (base + b * stride) * PK, w);
-#pragma unroll
-        for (int q = 0; q < 9; ++q) ds[q] += Drow[b] * w[q];
-      }
-      Real G[9];
-      apply_Apos(m1, m2, m3, ds, G);
-#pragma unroll
-      for (int q = 0; q < 9; ++q) acc[q] += G[q];
+      __syncthreads();
     }
-    __syncthreads();
   }
 
   // Face items: lifted flux differences (x_s now aliases the free flux tile).
@@ -324,10 +381,10 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
         for (int q = 0; q < 9; ++q) du[q] = um[q];
       }
       const Real sgn = hi ? Real(1) : Real(-1);
-      const Real m1 = sgn * g_s[sidx * PK + 3 * d + 0];
-      const Real m2 = sgn * g_s[sidx * PK + 3 * d + 1];
-      const Real m3 = sgn * g_s[sidx * PK + 3 * d + 2];
-      const Real jv = g_s[sidx * PK + 9];
+      const Real m1 = sgn * g_s[sidx * PK + gslot<Real>(d, 0)];
+      const Real m2 = sgn * g_s[sidx * PK + gslot<Real>(d, 1)];
+      const Real m3 = sgn * g_s[sidx * PK + gslot<Real>(d, 2)];
+      const Real jv = g_s[sidx * PK + gslot_ij<Real>()];
 
       Real Ad[9];
       apply_Apos(m1, m2, m3, du, Ad);      // A_+(m) du = -A(m) du
@@ -412,7 +469,7 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
   if (active) {
     // vol = -1/2 (1/J) (-acc_+) = +1/2 (1/J) acc_+  (acc holds A_+ terms)
     Real r[9];
-    const Real hv = static_cast<Real>(0.5) * g_s[t * PK + 9];
+    const Real hv = static_cast<Real>(0.5) * g_s[t * PK + gslot_ij<Real>()];
 #pragma unroll
     for (int q = 0; q < 9; ++q) r[q] = hv * sgnA * acc[q];
     const int fb0 = el * 6 * nf;
