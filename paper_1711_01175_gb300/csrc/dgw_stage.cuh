@@ -110,10 +110,6 @@ struct Pack<double> {
   }
 };
 
-__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
-  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gsrc) : "memory");
-}
 // Hint: bring [lo, hi) (rounded out to 16 B) into L2 with one bulk prefetch.
 // Callers keep the rounded range inside the buffer.
 __device__ __forceinline__ void prefetch_l2(const void* lo, const void* hi) {
@@ -121,25 +117,22 @@ __device__ __forceinline__ void prefetch_l2(const void* lo, const void* hi) {
   const unsigned long long b = (reinterpret_cast<unsigned long long>(hi) + 15ull) & ~15ull;
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(a), "r"((unsigned)(b - a)) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 template <int N, typename Real>
 struct StageSmem {
   using S = Shape<N>;
   static constexpr int PK = Pack<Real>::PK;
-  static constexpr bool kPrefetchRes = std::is_same<Real, float>::value;
   static constexpr size_t u_off = 0;                                    // Real [NTILE][PK] state
   static constexpr size_t f_off = u_off + sizeof(Real) * S::NTILE * PK;  // Real [NTILE][PK] flux / face fluxes
   // FP64 stages A(Ja^i)u in this region before the face fluxes reuse it; FP32
   // recomputes A(Ja^i)u at the contraction nodes and keeps only the face fluxes.
-  static constexpr size_t fwords = (kPrefetchRes || S::NTILE * PK < 9 * S::NFACE_ITEMS) ? 9 * S::NFACE_ITEMS : S::NTILE * PK;
+  static constexpr size_t fwords =
+      (std::is_same<Real, float>::value || S::NTILE * PK < 9 * S::NFACE_ITEMS) ? 9 * S::NFACE_ITEMS : S::NTILE * PK;
   static constexpr size_t fbytes = sizeof(Real) * fwords;
   static constexpr size_t g_off = f_off + ((fbytes + 15) / 16) * 16;     // Real [NTILE][PK] Ja, 1/J
   static constexpr size_t d_off = g_off + sizeof(Real) * S::NTILE * PK;  // Real [n*n]
   static constexpr size_t e_off = ((d_off + sizeof(Real) * S::n * S::n + 15) / 16) * 16;  // double [32] reduction
-  static constexpr size_t r_off = e_off + sizeof(double) * 32;                            // double [9][NTILE]
-  static constexpr size_t bytes = r_off + (kPrefetchRes ? sizeof(double) * 9 * S::NTILE : 0);
+  static constexpr size_t bytes = e_off + sizeof(double) * 32;
 };
 
 // Slots of the metric terms in a node's geometry tile: Ja^dir_k and 1/J.  FP32
@@ -173,14 +166,12 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
   using V = Pack<Real>;
   constexpr int n = S::n, Np = S::Np, nf = S::nf, EPB = S::EPB, NT = S::NT;
   constexpr int NTILE = S::NTILE, NFI = S::NFACE_ITEMS, PK = L::PK;
-  constexpr bool kPrefetch = LSRK && L::kPrefetchRes;
 
   Real* u_s = reinterpret_cast<Real*>(smem_raw + L::u_off);
   Real* f_s = reinterpret_cast<Real*>(smem_raw + L::f_off);
   Real* x_s = f_s;                       // face fluxes [9][NFI] reuse the flux tile
   Real* g_s = reinterpret_cast<Real*>(smem_raw + L::g_off);
   Real* D_s = reinterpret_cast<Real*>(smem_raw + L::d_off);
-  double* r_s = reinterpret_cast<double*>(smem_raw + L::r_off);
   double* red_s = reinterpret_cast<double*>(smem_raw + L::e_off);
 
   const int t = threadIdx.x;
@@ -214,14 +205,6 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
         prefetch_l2(a, a + len);
       }
     }
-  }
-  if constexpr (kPrefetch) {
-    // The register res is needed only in the epilogue: start its copy now.
-    if (active && !first) {
-#pragma unroll
-      for (int q = 0; q < 9; ++q) cp_async8(&r_s[q * NTILE + t], &p.res[q * fstride + gidx]);
-    }
-    cp_async_commit();
   }
 
   if (in_tile) {
@@ -543,7 +526,6 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
     } else {
       // res <- a res + dt rhs; u_out <- u_in + b res, both FP64.  a_0 = 0: the
       // incoming register is not read in the first stage.
-      if constexpr (kPrefetch) cp_async_wait_all();
       double uout[9];
 #pragma unroll
       for (int q = 0; q < 9; ++q) {
@@ -554,14 +536,7 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
         } else {
           dtr = widen_int(static_cast<float>(p.dt) * rr[q]);
         }
-        double rin = 0.0;
-        if (!first) {
-          if constexpr (kPrefetch) {
-            rin = r_s[q * NTILE + t];
-          } else {
-            rin = p.res[q * fstride + gidx];
-          }
-        }
+        const double rin = first ? 0.0 : p.res[q * fstride + gidx];
         const double rn = first ? dtr : fma(p.a, rin, dtr);
         p.res[q * fstride + gidx] = rn;
         const double uo = fma(p.b, rn, uq);
