@@ -146,6 +146,8 @@ dgw_status dgw_batch_create(dgw_batch** out, int device, int N, int precision, i
   dgw::RefElem R;
   dgw::build_ref_elem(N, &R);
   L.w_end_inv = 1.0 / R.w[0];
+  L.tau_f = static_cast<float>(L.tau);
+  L.hlift_f = static_cast<float>(0.5 * L.w_end_inv);
   for (int i = 0; i < (N + 1) * (N + 1); ++i) L.D[i] = R.D[i];
   L.pf_elems = 2LL * b->sm_count * epb;
   cudaStream_t cs = b->capture;
@@ -158,6 +160,7 @@ dgw_status dgw_batch_create(dgw_batch** out, int device, int N, int precision, i
       L.a = dgw::kA[st];
       L.b = dgw::kB[st];
       L.c = dgw::kC[st];
+      L.first = st == 0 ? 1 : 0;
       e = dgw::launch_stage_batch(N, precision == DGW_PRECISION_MIXED, L, b->set, 1, cs);
     }
   }
@@ -236,6 +239,7 @@ dgw_status dgw_batch_set(dgw_batch* b, int n, dgw_ctx* const* ctxs, double* cons
     d.mat = c->mat;
     d.nel = c->nel;
     d.dt = dt[i];
+    d.dt_f = static_cast<float>(dt[i]);
     d.src_elem = c->src_elem;
     d.src_w = c->src_w;
     d.src_f0 = c->src_f0;

@@ -64,8 +64,20 @@ struct StageParams {
   long long src_elem;       // element holding the point force, -1 for none
   double src_amp;           // Ricker amplitude R(t + c_s dt) of this stage
   const double* src_w;      // [3][Np]: F_q l_j(xi_s) / (rho w_j J_j)
+  // FP32 copies of dt, tau and w_end_inv / 2, and a == 0, set by the launcher so
+  // that the FP32 path reads them from the constant bank without conversions.
+  float dt_f, tau_f, hlift_f;
+  int first;
   double D[(kMaxN + 1) * (kMaxN + 1)];
 };
+
+// Fill the FP32 copies of a stage's scalar parameters.
+inline void finish_stage_params(StageParams& p) {
+  p.dt_f = static_cast<float>(p.dt);
+  p.tau_f = static_cast<float>(p.tau);
+  p.hlift_f = static_cast<float>(0.5 * p.w_end_inv);
+  p.first = p.a == 0.0 ? 1 : 0;
+}
 
 // Solves per batch.  Their descriptors travel in the stage kernel's parameters
 // (constant bank: uniform, re-loadable, no registers held across the tile).
@@ -81,6 +93,7 @@ struct BatchSolve {
   const void* mat;
   long long nel;
   double dt;
+  float dt_f;             // FP32 copy of dt
   long long src_elem;
   const double* src_w;
   double src_f0, src_t0;
@@ -102,6 +115,8 @@ struct BatchLaunch {
   double a, b, c;         // LSRK coefficients of this stage
   double tau;
   double w_end_inv;
+  float tau_f, hlift_f;   // FP32 copies of tau and w_end_inv / 2
+  int first;              // a == 0
   long long pf_elems;
   double D[(kMaxN + 1) * (kMaxN + 1)];
 };

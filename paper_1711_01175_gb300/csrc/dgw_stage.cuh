@@ -20,6 +20,7 @@
 //      res <- a res + dt rhs, u_out <- u_in + b res in FP64.
 #pragma once
 
+#include <atomic>
 #include <type_traits>
 
 #include "dgw_internal.cuh"
@@ -60,6 +61,16 @@ __device__ __forceinline__ double widen_int(float x) {
   unsigned long long mag = static_cast<unsigned long long>(u & 0x7fffffffu) << 29;
   mag = (e == 255u) ? (mag | 0x7ff0000000000000ull) : (mag + (896ull << 52));
   return __longlong_as_double(static_cast<long long>(e == 0u ? sign : (sign | mag)));
+}
+
+// A scalar parameter in the path's precision: the double, or its FP32 copy.
+template <typename Real>
+__device__ __forceinline__ Real pick(double d, float f) {
+  if constexpr (std::is_same<Real, double>::value) {
+    return d;
+  } else {
+    return f;
+  }
 }
 
 template <typename Real>
@@ -184,7 +195,7 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
   const size_t fstride = static_cast<size_t>(p.nel) * Np;
   const size_t gidx = active ? static_cast<size_t>(e) * Np + node : 0;
   const Real* geo = static_cast<const Real*>(p.geo);
-  const bool first = p.a == 0.0;
+  const bool first = p.first != 0;
 
   if (p.pf_elems > 0) {
     // L2 prefetch of the tile that starts about two CTAs per SM later, so that its
@@ -328,8 +339,8 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
   // Face items: lifted flux differences (x_s now aliases the free flux tile).
   {
     const Real* fz = static_cast<const Real*>(p.fz);
-    const Real tau = static_cast<Real>(p.tau);
-    const Real half_lift = static_cast<Real>(0.5 * p.w_end_inv);
+    const Real tau = pick<Real>(p.tau, p.tau_f);
+    const Real half_lift = pick<Real>(0.5 * p.w_end_inv, p.hlift_f);
     for (int it = t; it < NFI; it += NT) {
       const int eli = it / (6 * nf);
       const int r = it - eli * (6 * nf);
@@ -534,7 +545,7 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
         if constexpr (std::is_same<Real, double>::value) {
           dtr = p.dt * rr[q];
         } else {
-          dtr = widen_int(static_cast<float>(p.dt) * rr[q]);
+          dtr = widen_int(p.dt_f * rr[q]);
         }
         const double rin = first ? 0.0 : p.res[q * fstride + gidx];
         const double rn = first ? dtr : fma(p.a, rin, dtr);
@@ -592,7 +603,7 @@ template <int N, typename Real, int MODE>
 __global__ void __launch_bounds__(Shape<N>::NT) stage_kernel(const StageParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* D_s = reinterpret_cast<Real*>(smem_raw + StageSmem<N, Real>::d_off);
-  for (int i = threadIdx.x; i < Shape<N>::n * Shape<N>::n; i += Shape<N>::NT) D_s[i] = static_cast<Real>(p.D[i]);
+  for (int i = threadIdx.x; i < Shape<N>::n * Shape<N>::n; i += Shape<N>::NT) D_s[i] = to_real<Real>(p.D[i]);
   stage_tile<N, Real, MODE>(p, blockIdx.x, smem_raw);
 }
 
@@ -615,7 +626,7 @@ __global__ void __launch_bounds__(Shape<N>::NT) stage_batch_kernel(const BatchLa
   const long long tile = blockIdx.x;
   if (tile >= S.total_tiles) return;
   Real* D_s = reinterpret_cast<Real*>(smem_raw + StageSmem<N, Real>::d_off);
-  for (int i = threadIdx.x; i < Shape<N>::n * Shape<N>::n; i += Shape<N>::NT) D_s[i] = static_cast<Real>(L.D[i]);
+  for (int i = threadIdx.x; i < Shape<N>::n * Shape<N>::n; i += Shape<N>::NT) D_s[i] = to_real<Real>(L.D[i]);
   int lo = 0, hi = S.nsolves - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) / 2;
@@ -644,6 +655,10 @@ __global__ void __launch_bounds__(Shape<N>::NT) stage_batch_kernel(const BatchLa
   ps.grad_face = nullptr;
   ps.src_elem = b.src_elem;
   ps.src_w = b.src_w;
+  ps.dt_f = b.dt_f;
+  ps.tau_f = L.tau_f;
+  ps.hlift_f = L.hlift_f;
+  ps.first = L.first;
   ps.src_amp = 0.0;
   if (b.src_elem >= 0 && b.src_elem / Shape<N>::EPB == tile - b.tile0)
     ps.src_amp = ricker_dev(L.times[lo] + (L.step + L.c) * b.dt, b.src_f0, b.src_t0);
@@ -698,15 +713,25 @@ template <int N, typename Real, int MODE>
 cudaError_t launch_stage_t(const StageParams& p, cudaStream_t s) {
   using S = Shape<N>;
   const size_t smem = StageSmem<N, Real>::bytes;
-  cudaError_t err = cudaFuncSetAttribute(stage_kernel<N, Real, MODE>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // Kernel attributes, set once per device (bit d of `ready`; devices 0..63).
+  static std::atomic<unsigned long long> ready{0};
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
   if (err != cudaSuccess) return err;
-  err = cudaFuncSetAttribute(stage_kernel<N, Real, MODE>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             (int)cudaSharedmemCarveoutMaxShared);
-  if (err != cudaSuccess) return err;
+  const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
+  if (!(ready.load(std::memory_order_relaxed) & bit)) {
+    err = cudaFuncSetAttribute(stage_kernel<N, Real, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    err = cudaFuncSetAttribute(stage_kernel<N, Real, MODE>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               (int)cudaSharedmemCarveoutMaxShared);
+    if (err != cudaSuccess) return err;
+    ready.fetch_or(bit, std::memory_order_relaxed);
+  }
   const long long blocks = (p.nel + S::EPB - 1) / S::EPB;
   if (blocks <= 0) return cudaSuccess;
-  stage_kernel<N, Real, MODE><<<(unsigned)blocks, S::NT, smem, s>>>(p);
+  StageParams q = p;
+  finish_stage_params(q);
+  stage_kernel<N, Real, MODE><<<(unsigned)blocks, S::NT, smem, s>>>(q);
   return cudaGetLastError();
 }
 

@@ -3,7 +3,9 @@
 Each solve in a batch must end where the single-solve path (dgw_step) ends,
 and the batch may change composition between step pairs.  The arithmetic per
 element is the same; the source amplitude comes from a device-side time in the
-batch, so results agree to rounding, not bit for bit.
+batch, so results agree to rounding, not bit for bit: 1e-13 relative L2 for
+FP64, 1e-6 for the mixed path (where the amplitude differs in its last bit,
+the FP32 rounding of the point force can flip).
 """
 import ctypes
 
@@ -16,7 +18,7 @@ from harness import rel_l2
 
 pytestmark = pytest.mark.gpu
 
-BATCH_TOL = 1e-13
+BATCH_TOL = {"fp64": 1e-13, "mixed": 1e-6}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -94,10 +96,11 @@ def test_batch_matches_single_solves_with_composition_change(precision):
     b.set(cont, [4 * items[0]["dt"], 4 * items[2]["dt"], 0.0], stream)       # no new graph: uploads only
     b.run(2, stream)
     torch.cuda.synchronize()
-    assert rel_l2(got_left, alone(left, 4)) < BATCH_TOL
-    assert rel_l2(items[0]["u"].cpu().numpy(), alone(items[0], 8)) < BATCH_TOL
-    assert rel_l2(items[2]["u"].cpu().numpy(), alone(items[2], 8)) < BATCH_TOL
-    assert rel_l2(late["u"].cpu().numpy(), alone(late, 4)) < BATCH_TOL
+    tol = BATCH_TOL[precision]
+    assert rel_l2(got_left, alone(left, 4)) < tol
+    assert rel_l2(items[0]["u"].cpu().numpy(), alone(items[0], 8)) < tol
+    assert rel_l2(items[2]["u"].cpu().numpy(), alone(items[2], 8)) < tol
+    assert rel_l2(late["u"].cpu().numpy(), alone(late, 4)) < tol
     b.close()
 
 
