@@ -41,17 +41,45 @@ __device__ __forceinline__ void apply_Apos(Real m1, Real m2, Real m3, const Real
   out[8] = m1 * w[1] + m2 * w[0];
 }
 
-// FP64 -> FP32 (round to nearest on the dropped 29 bits, flush below the
-// smallest normal float) and FP32 -> FP64 (exact) with integer instructions.
-// The GB300 FP64 pipe, which also executes the F2F conversions, issues about
-// two operations per clock per SM; integer operations are much wider.
+// acc += A_+(m) w.
+template <typename Real>
+__device__ __forceinline__ void acc_Apos(Real m1, Real m2, Real m3, const Real* w, Real* acc) {
+  acc[0] += m1 * w[3];
+  acc[0] += m2 * w[8];
+  acc[0] += m3 * w[7];
+  acc[1] += m1 * w[8];
+  acc[1] += m2 * w[4];
+  acc[1] += m3 * w[6];
+  acc[2] += m1 * w[7];
+  acc[2] += m2 * w[6];
+  acc[2] += m3 * w[5];
+  acc[3] += m1 * w[0];
+  acc[4] += m2 * w[1];
+  acc[5] += m3 * w[2];
+  acc[6] += m2 * w[2];
+  acc[6] += m3 * w[1];
+  acc[7] += m1 * w[2];
+  acc[7] += m3 * w[0];
+  acc[8] += m1 * w[1];
+  acc[8] += m2 * w[0];
+}
+
+// FP64 -> FP32 (round half up on the 29 dropped mantissa bits, flush below
+// the smallest normal float, overflow to infinity) and FP32 -> FP64 (exact)
+// with integer instructions.  The GB300 FP64 pipe, which also executes the
+// F2F conversions, issues about two operations per clock per SM; integer
+// operations are much wider.  Narrowing works on the two 32-bit halves: a
+// funnel shift lines up the low 9 exponent bits and the top 23 mantissa bits,
+// and subtracting 0x180 << 23 rebiases the exponent (1023 - 127 = 896 = 0x380,
+// which is 0x180 modulo 2^9) wherever the result is a normal float.
 __device__ __forceinline__ float narrow_int(double d) {
-  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(d));
-  const unsigned sign = static_cast<unsigned>(b >> 32) & 0x80000000u;
-  const unsigned long long mag = b & 0x7fffffffffffffffull;
-  long long f = static_cast<long long>((mag + (1ull << 28)) >> 29) - (896ll << 23);
-  f = f < (1ll << 23) ? 0ll : (f > 0x7f800000ll ? 0x7f800000ll : f);
-  return __uint_as_float(static_cast<unsigned>(f) | sign);
+  const unsigned hi = static_cast<unsigned>(__double2hiint(d));
+  const unsigned lo = static_cast<unsigned>(__double2loint(d));
+  const unsigned ahi = hi & 0x7fffffffu;
+  unsigned f = __funnelshift_l(lo, ahi, 3) - 0xC0000000u + ((lo >> 28) & 1u);
+  const unsigned e11 = ahi >> 20;
+  f = (e11 - 897u <= 253u) ? f : (e11 < 897u ? 0u : 0x7f800000u);
+  return __uint_as_float(f | (hi & 0x80000000u));
 }
 
 __device__ __forceinline__ double widen_int(float x) {
@@ -266,15 +294,13 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
         for (int b = 0; b < n; ++b) {
           const Real Dab = D_s[a * n + b];
           const int nb = base + b * stride;
-          Real w[10], F[9];
+          Real w[10];
           V::load9(u_s + nb * PK, w);
           const float4 mb = reinterpret_cast<const float4*>(g_s + nb * PK)[dir];
-          apply_Apos(mb.x, mb.y, mb.z, w, F);
+          // D_ab A_+(m_b) u_b = A_+(D_ab m_b) u_b, accumulated term by term
+          acc_Apos(Dab * mb.x, Dab * mb.y, Dab * mb.z, w, acc);
 #pragma unroll
-          for (int q = 0; q < 9; ++q) {
-            acc[q] += Dab * F[q];
-            ds[q] += Dab * w[q];
-          }
+          for (int q = 0; q < 9; ++q) ds[q] += Dab * w[q];
         }
         const float4 mt = reinterpret_cast<const float4*>(g_s + t * PK)[dir];
         Real G[9];
