@@ -8,3 +8,4 @@ from .dg_elastic import (ElasticDG, gll, lagrange_derivative_matrix, legendre, A
                          Q_of, stiffness_voigt, weighted_trace, hdg_flux, LSRK_A, LSRK_B, LSRK_C,
                          cfl_dt, cfl_number, face_node_indices, neighbour_face_position,
                          h_min_corner_edges, ricker, lagrange_values)
+from .dg_friedrichs import FriedrichsSystem, FriedrichsDG, transport, shallow_water

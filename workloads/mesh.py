@@ -33,6 +33,7 @@ import numpy as np
 
 BC_INTERIOR = 0       # interior or periodic face: neighbour via etoe/etof/orient
 BC_FREE_SURFACE = 1   # traction-free surface
+BC_WALL = 1           # the same tag for the shallow-water system: reflecting wall
 BC_ABSORBING = 2      # zero exterior state
 
 _TANGENTS = {0: (1, 2), 1: (0, 2), 2: (0, 1)}
