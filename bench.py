@@ -408,6 +408,76 @@ def run_adjoint(args):
             "gradient_norm": float(np.linalg.norm(g)), "precision": "fp64"}
 
 
+def friedrichs_flops_per_node(system, N):
+    """FP64 flops of one stage per node as the generic kernel's arithmetic is
+    written (n = N + 1; 6 n^2 / n^3 face items per node):
+    transport   volume 3 (A(m)u 6 + two length-n contractions 4n + A(m) du 6 + 2),
+                face item 18, RK update, lift and fused energy 10;
+    shallow water  volume 3 (5 + 12n + 5 + 6), face item 25, update 25."""
+    n = N + 1
+    per_face = 6.0 * n * n / n ** 3
+    if system == "transport":
+        return 3 * (14 + 4 * n) + per_face * 18 + 10
+    return 3 * (16 + 12 * n) + per_face * 25 + 25
+
+
+def run_friedrichs(args, hbm_peak, peak_kind):
+    """The generic Friedrichs systems (FP64): transport (beta = (0.2, 0.2, 0.2),
+    the velocity of the paper's 3-D transport test) on the 64^3, N=4 warped
+    periodic mesh, and the shallow-water standing wave with walls on a
+    512 x 512 x 1, N=4 mesh.  K steps of dgw_step timed with CUDA events
+    (inputs larger than L2); algorithmic bytes per DOF and stage: the FP64 state
+    (u and res in and out, 32 B; 24 B in stage 0) plus 10 FP64 geometry values
+    per node shared by the m fields."""
+    import torch
+    from paper_1711_01175_gb300 import Solver, reference_nodes
+    N = 4
+    r, _ = reference_nodes(N)
+    out = {}
+    cases = [("transport", wl.structured_hex_mesh(args.fr_E, order="morton"), 0.1),
+             ("shallow_water", wl.structured_hex_mesh((8 * args.fr_E, 8 * args.fr_E, 1), (False, False, True),
+                                                     {0: wl.BC_WALL, 1: wl.BC_WALL, 2: wl.BC_WALL, 3: wl.BC_WALL},
+                                                     order="morton"), 0.0)]
+    stream = torch.cuda.Stream()
+    for system, mesh, amp in cases:
+        x = wl.warped_node_coords(mesh, r, amp)
+        s = Solver(N, system=system, beta=(0.2, 0.2, 0.2))
+        s.upload_mesh(x, mesh.etoe, mesh.etof, mesh.orient, mesh.bc)
+        u0 = wl.transport_periodic(x, (0.2, 0.2, 0.2)) if system == "transport" else wl.shallow_water_standing_wave(x)
+        m = u0.shape[0]
+        dt = s.dt_cfl()
+        with torch.cuda.stream(stream):
+            u = torch.from_numpy(u0).cuda()
+            res = torch.zeros_like(u)
+            s.step(u, res, dt, args.warmup, stream=stream)
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            s.step(u, res, dt, args.fr_steps, stream=stream)
+            t1.record(stream)
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1)
+        e = s.energy(u)
+        nodes = mesh.nel * (N + 1) ** 3
+        dof_stages = nodes * m * 5 * args.fr_steps
+        bytes_step = nodes * (m * (24 + 4 * 32) + 5 * 80)
+        gbs = bytes_step * args.fr_steps / (ms * 1e-3) / 1e9
+        tf = friedrichs_flops_per_node(system, N) * nodes * 5 * args.fr_steps / (ms * 1e-3) / 1e12
+        out[system] = {"mesh": "x".join(str(v) for v in mesh.E), "N": N, "m": m, "dof": nodes * m,
+                       "steps": args.fr_steps, "ms_per_step": ms / args.fr_steps,
+                       "value": dof_stages / (ms * 1e-3), "unit": UNIT, "dtype": "f64",
+                       "roofline": {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                    "frac": tf / FP64_PEAK_TFLOPS,
+                                    "note": f"FP64 flops as written ({friedrichs_flops_per_node(system, N):.0f} per "
+                                            f"node and stage) / CUDA-event time; HBM: {gbs:.0f} GB/s = "
+                                            f"{gbs / hbm_peak:.3f} of {peak_kind} copy bandwidth at "
+                                            f"{bytes_step / (5 * nodes * m):.1f} algorithmic B/DOF per stage"},
+                       "energy_end": e}
+        s.close()
+        del u, res
+    return out
+
+
 def build_workload_oracle(name, E=None):
     import oracle
     cfg = workload_config(name, E)
@@ -431,6 +501,9 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=256, help="elements per reference-arm step")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-friedrichs", action="store_true", help="skip the transport / shallow-water section")
+    ap.add_argument("--fr-E", type=int, default=64, help="transport mesh edge (shallow water: 8x this, one layer)")
+    ap.add_argument("--fr-steps", type=int, default=20)
     ap.add_argument("--adj-E", type=int, default=16, help="adjoint mesh edge (the full recipe: 32)")
     ap.add_argument("--adj-steps", type=int, default=40, help="(the full recipe: 500)")
     ap.add_argument("--adj-receivers", type=int, default=8, help="(the full recipe: 32)")
@@ -538,6 +611,9 @@ def main():
         line["serving"] = run_serving(args)
     if world == 1 and not args.no_adjoint:
         line["adjoint"] = run_adjoint(args)
+    if world == 1 and not args.no_friedrichs:
+        hbm_peak_f, peak_kind_f = peaks()
+        line["friedrichs"] = run_friedrichs(args, hbm_peak_f, peak_kind_f)
     if len(results) > 1:
         m = results["mixed"]
         line["variants"] = {"mixed": {"value": m["value"], "dtype": "f32/f64", "steps": m["steps"],

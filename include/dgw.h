@@ -2,10 +2,14 @@
  * dgw.h -- C ABI of the GB300 DG elastic-wave hot path.
  *
  * The library evaluates the semi-discrete upwind DG operator of a linear
- * Friedrichs system (the paper's Section 2, eq. LPDE, with m = 9 unknowns:
- * velocity-stress elasticity, Q du/dt + sum_k d_k(A_k u) = 0) on curvilinear
- * hexahedra, and advances it with a five-stage low-storage Runge-Kutta
- * method.  The numerical flux is the upwind HDG flux (eq. RiemannFluxBoth)
+ * Friedrichs system (the paper's Section 2, eq. LPDE: Q du/dt +
+ * sum_k d_k(A_k u) = 0) on curvilinear hexahedra, and advances it with a
+ * five-stage low-storage Runge-Kutta method.  Three systems are built
+ * (dgw_config.system): velocity-stress elasticity (m = 9 unknowns, the
+ * medium in Q; the hot path), scalar transport (m = 1, A_k = beta_k, Q = 1;
+ * Section 6.1) and the linearized shallow-water system of
+ * eq. linearizedShallow with Phi = 1 and no Coriolis force, friction or wind
+ * stress (m = 3, u = (phi, Phi u, Phi v), Q = I, A_3 = 0; Section 6.3).  The numerical flux is the upwind HDG flux (eq. RiemannFluxBoth)
  * with the trace eliminated through the face conservation condition
  * (eq. HDGeqn, in the form of eq. iHDGtrace); the time scheme is the paper's
  * element-by-element explicit HDG scheme (Section 4.2) with LSRK(5,4) in place
@@ -17,7 +21,9 @@
  *        Np = n^3 nodes per element, nf = n^2 nodes per face.
  * node   index i + n*(j + n*k) of reference node (r_i, s_j, t_k); r fastest.
  * faces  0: r=-1, 1: r=+1, 2: s=-1, 3: s=+1, 4: t=-1, 5: t=+1.
- * state  u[9][nel][Np], FP64, fields (v1, v2, v3, s11, s22, s33, s23, s13, s12).
+ * state  u[m][nel][Np], FP64.  Elastic: m = 9, fields (v1, v2, v3, s11, s22,
+ *        s33, s23, s13, s12); transport: m = 1; shallow water: m = 3,
+ *        (phi, Phi u, Phi v).  Below, [9] reads [m] for the other systems.
  *
  * Errors: every call returns a dgw_status and never aborts or throws.  A
  * failing call leaves a message retrievable with dgw_last_error(ctx).  Calls
@@ -52,19 +58,31 @@ typedef enum {
 } dgw_status;
 
 enum { DGW_PRECISION_FP64 = 0, DGW_PRECISION_MIXED = 1 };
-enum { DGW_BC_INTERIOR = 0, DGW_BC_FREE_SURFACE = 1, DGW_BC_ABSORBING = 2 };
+/* Boundary tags.  1 is the traction-free surface of the elastic system
+ * (exterior state (v, -sigma)) and the reflecting wall of the shallow-water
+ * system (exterior state (phi, q - 2 (q.n) n), q the momentum, n the
+ * horizontal part of the unit normal); it is refused for transport.  2 is a
+ * zero exterior state for every system (absorbing for elasticity, zero
+ * inflow for transport). */
+enum { DGW_BC_INTERIOR = 0, DGW_BC_FREE_SURFACE = 1, DGW_BC_WALL = 1, DGW_BC_ABSORBING = 2 };
+enum { DGW_SYSTEM_ELASTIC = 0, DGW_SYSTEM_TRANSPORT = 1, DGW_SYSTEM_SHALLOW_WATER = 2 };
 
 typedef struct {
   int N;          /* polynomial degree, 1..7 */
   int flux_tau;   /* 0: central flux (stabilisation dropped), 1: upwind HDG flux */
   int precision;  /* DGW_PRECISION_FP64: every operation in FP64.
                      DGW_PRECISION_MIXED: volume, flux and lift in FP32 with FP32
-                     geometry; the Runge-Kutta registers and energy stay FP64. */
+                     geometry; the Runge-Kutta registers and energy stay FP64.
+                     Elastic system only. */
   double cfl;     /* CFL number used by dgw_dt_cfl */
+  int system;     /* DGW_SYSTEM_*.  Transport and shallow water: FP64 only, no
+                     material (Q = I), no point force, receivers, adjoint or
+                     batches (those calls return DGW_ERR_UNSUPPORTED). */
+  double beta[3]; /* transport velocity (DGW_SYSTEM_TRANSPORT); ignored otherwise */
 } dgw_config;
 
 /* ABI version of this header (bumped on any signature change). */
-#define DGW_ABI_VERSION 6
+#define DGW_ABI_VERSION 7
 int dgw_abi_version(void);
 
 /* GLL nodes r[0..N] (ascending, r[0] = -1, r[N] = +1) and weights w[0..N]
@@ -96,20 +114,22 @@ dgw_status dgw_destroy(dgw_ctx* ctx);
  *          (a1, b1) = (o & 1) ? (b, a) : (a, b), a' = (o & 2) ? N - a1 : a1,
  *          b' = (o & 4) ? N - b1 : b1;
  *   bc     [nel][6] DGW_BC_INTERIOR where etoe >= 0, otherwise
- *          DGW_BC_FREE_SURFACE (traction-free: exterior state (v, -sigma)) or
+ *          DGW_BC_FREE_SURFACE / DGW_BC_WALL (see the boundary tags above) or
  *          DGW_BC_ABSORBING (exterior state 0).
  * The call computes the curl-form metric terms, Jacobians, face normals and
  * face stabilisation matrices on the device.  DGW_ERR_ARG (message names the
  * element) if the connectivity is not symmetric, a tag is inconsistent, or
  * J <= 0 at some node; nel * Np must be below 2^31.  May be called again to
- * replace the mesh (material must then be uploaded again). */
+ * replace the mesh (material must then be uploaded again).  For transport and
+ * shallow water the context is ready for compute calls after this call. */
 dgw_status dgw_mesh_upload(dgw_ctx* ctx, int64_t nel, const double* x, const int64_t* etoe,
                            const int8_t* etof, const int8_t* orient, const int8_t* bc);
 
 /* Per-element isotropic medium: density rho, Lame parameters lam and mu (host
  * [nel] arrays, caller-owned).  The medium enters only the time weight
  * Q = diag(rho I, C_V^{-1}).  DGW_ERR_ARG unless rho > 0, mu > 0 and
- * lam > -2/3 mu everywhere.  DGW_ERR_STATE before dgw_mesh_upload. */
+ * lam > -2/3 mu everywhere.  DGW_ERR_STATE before dgw_mesh_upload.
+ * DGW_ERR_UNSUPPORTED for transport and shallow water (Q = I). */
 dgw_status dgw_material_upload(dgw_ctx* ctx, const double* rho, const double* lam, const double* mu);
 
 /* rhs = L(u) = Q^{-1} [ split-form volume term + lifted upwind flux

@@ -19,11 +19,13 @@ DGW_PRECISION_FP64 = 0
 DGW_PRECISION_MIXED = 1
 DGW_BC_INTERIOR, DGW_BC_FREE_SURFACE, DGW_BC_ABSORBING = 0, 1, 2
 DGW_BATCH_MAX_SOLVES = 128
+DGW_SYSTEM_ELASTIC, DGW_SYSTEM_TRANSPORT, DGW_SYSTEM_SHALLOW_WATER = 0, 1, 2
+DGW_BC_WALL = 1
 
 
 class dgw_config(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int), ("flux_tau", ctypes.c_int), ("precision", ctypes.c_int),
-                ("cfl", ctypes.c_double)]
+                ("cfl", ctypes.c_double), ("system", ctypes.c_int), ("beta", ctypes.c_double * 3)]
 
 
 _P = ctypes.c_void_p

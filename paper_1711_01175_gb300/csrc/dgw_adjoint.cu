@@ -200,6 +200,7 @@ extern "C" {
 
 dgw_status dgw_receivers_set(dgw_ctx* c, int n, const int64_t* elements, const double* xi) {
   if (!c) return afail(nullptr, DGW_ERR_ARG, "null context");
+  if (c->cfg.system != DGW_SYSTEM_ELASTIC) return afail(c, DGW_ERR_UNSUPPORTED, "receivers are elastic only");
   if (!c->has_mesh) return afail(c, DGW_ERR_STATE, "receivers before mesh");
   if (n < 0 || (n > 0 && (!elements || !xi))) return afail(c, DGW_ERR_ARG, "bad receiver arrays");
   const int N = c->cfg.N, nn = N + 1, Np = nn * nn * nn;
@@ -265,6 +266,7 @@ dgw_status dgw_receivers_adjoint(dgw_ctx* c, double* lam_u, const double* gv, vo
 dgw_status dgw_adjoint_step(dgw_ctx* c, double* lam_u, double* lam_res, double* grad_mat, const double* u_ckpt,
                             double t0, double dt, int nsteps, void* stream) {
   if (!c) return afail(nullptr, DGW_ERR_ARG, "null context");
+  if (c->cfg.system != DGW_SYSTEM_ELASTIC) return afail(c, DGW_ERR_UNSUPPORTED, "the adjoint is elastic only");
   if (!c->has_mesh || !c->has_material) return afail(c, DGW_ERR_STATE, "adjoint before mesh and material");
   if (c->cfg.precision != DGW_PRECISION_FP64)
     return afail(c, DGW_ERR_UNSUPPORTED, "the adjoint is built for FP64 contexts only");

@@ -224,6 +224,8 @@ dgw_status dgw_batch_set(dgw_batch* b, int n, dgw_ctx* const* ctxs, double* cons
   for (int i = 0; i < n; ++i) {
     dgw_ctx* c = ctxs[i];
     if (!c || !c->has_mesh || !c->has_material) return bfail(b, DGW_ERR_STATE, "solve without mesh or material");
+    if (c->cfg.system != DGW_SYSTEM_ELASTIC)
+      return bfail(b, DGW_ERR_UNSUPPORTED, "solve " + std::to_string(i) + ": batches hold elastic solves only");
     if (c->cfg.N != b->N || c->cfg.precision != b->precision || c->cfg.flux_tau != b->tau || c->device != b->device)
       return bfail(b, DGW_ERR_ARG, "solve " + std::to_string(i) + " differs in degree, precision, flux or device");
     if (!u[i] || !res[i] || u[i] == res[i] || !device_ptr(u[i]) || !device_ptr(res[i]))

@@ -126,9 +126,10 @@ dgw_status launch_stage(dgw_ctx* c, const double* u_in, double* out, double* res
   p.tau = c->cfg.flux_tau ? 1.0 : 0.0;
   p.w_end_inv = 1.0 / c->ref.w[0];
   std::memcpy(p.D, c->ref.D, sizeof(p.D));
-  cudaError_t e = c->cfg.precision == DGW_PRECISION_MIXED
-                      ? dgw::launch_stage_mixed(c->cfg.N, lsrk, p, s)
-                      : dgw::launch_stage_fp64(c->cfg.N, lsrk, p, s);
+  for (int k = 0; k < 3; ++k) p.beta[k] = c->cfg.beta[k];
+  cudaError_t e = c->cfg.system != DGW_SYSTEM_ELASTIC ? dgw::launch_friedrichs(c->cfg.system, c->cfg.N, lsrk, p, s)
+                  : c->cfg.precision == DGW_PRECISION_MIXED ? dgw::launch_stage_mixed(c->cfg.N, lsrk, p, s)
+                                                           : dgw::launch_stage_fp64(c->cfg.N, lsrk, p, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "stage kernel launch");
   return DGW_OK;
 }
@@ -244,6 +245,15 @@ dgw_status dgw_create(dgw_ctx** out, int device, const dgw_config* cfg) {
   if (cfg->precision != DGW_PRECISION_FP64 && cfg->precision != DGW_PRECISION_MIXED)
     return fail(nullptr, DGW_ERR_ARG, "unknown precision %d", cfg->precision);
   if (!(cfg->cfl > 0.0)) return fail(nullptr, DGW_ERR_ARG, "cfl must be positive");
+  if (cfg->system != DGW_SYSTEM_ELASTIC && cfg->system != DGW_SYSTEM_TRANSPORT &&
+      cfg->system != DGW_SYSTEM_SHALLOW_WATER)
+    return fail(nullptr, DGW_ERR_ARG, "unknown system %d", cfg->system);
+  if (cfg->system != DGW_SYSTEM_ELASTIC && cfg->precision != DGW_PRECISION_FP64)
+    return fail(nullptr, DGW_ERR_UNSUPPORTED, "transport and shallow water are built in FP64 only");
+  if (cfg->system == DGW_SYSTEM_TRANSPORT) {
+    const double b2 = cfg->beta[0] * cfg->beta[0] + cfg->beta[1] * cfg->beta[1] + cfg->beta[2] * cfg->beta[2];
+    if (!(b2 > 0.0) || !std::isfinite(b2)) return fail(nullptr, DGW_ERR_ARG, "transport needs a finite nonzero beta");
+  }
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
   if (e != cudaSuccess || device < 0 || device >= ndev)
@@ -252,6 +262,7 @@ dgw_status dgw_create(dgw_ctx** out, int device, const dgw_config* cfg) {
   dgw_ctx* c = new dgw_ctx();
   c->device = device;
   c->cfg = *cfg;
+  c->m = cfg->system == DGW_SYSTEM_ELASTIC ? 9 : (cfg->system == DGW_SYSTEM_TRANSPORT ? 1 : 3);
   dgw::build_ref_elem(cfg->N, &c->ref);
   if (cudaSetDevice(device) != cudaSuccess) {
     delete c;
@@ -308,6 +319,8 @@ dgw_status dgw_mesh_upload(dgw_ctx* c, int64_t nel, const double* x, const int64
       } else {
         if (bc[k] != DGW_BC_FREE_SURFACE && bc[k] != DGW_BC_ABSORBING)
           return fail(c, DGW_ERR_ARG, "element %lld face %d: boundary face without a boundary tag", (long long)e, f);
+        if (bc[k] == DGW_BC_FREE_SURFACE && c->cfg.system == DGW_SYSTEM_TRANSPORT)
+          return fail(c, DGW_ERR_ARG, "element %lld face %d: tag 1 (wall) is not defined for transport", (long long)e, f);
       }
     }
   }
@@ -387,13 +400,14 @@ dgw_status dgw_mesh_upload(dgw_ctx* c, int64_t nel, const double* x, const int64
   DGW_TRY(cudaMalloc(&D_d, sizeof(c->ref.D)), "alloc D");
   DGW_TRY(cudaMalloc(&w_d, sizeof(c->ref.w)), "alloc w");
   DGW_TRY(cudaMalloc(&c->vmapP, fnodes * sizeof(int)), "alloc neighbour map");
-  DGW_TRY(cudaMalloc(&c->u2, nodes * 9 * sizeof(double)), "alloc state buffer");
+  DGW_TRY(cudaMalloc(&c->u2, nodes * c->m * sizeof(double)), "alloc state buffer");
   DGW_TRY(cudaMalloc(&c->partials, (dgw::kEnergyBlocks + 1) * sizeof(double)), "alloc energy partials");
   {
     int epb = 0, nthreads = 0;
     dgw::stage_shape(N, &epb, &nthreads);
     c->stage_ctas = (int)((nel + epb - 1) / epb);
-    DGW_TRY(cudaMalloc(&c->stage_partials, ((size_t)c->stage_ctas + 1) * sizeof(double)), "alloc stage energy partials");
+    DGW_TRY(cudaMalloc(&c->stage_partials, ((size_t)c->stage_ctas + 1 + dgw::kEnergyBlocks) * sizeof(double)),
+            "alloc stage energy partials");
   }
   DGW_TRY(cudaMemcpyAsync(x_d, x, nodes * 3 * sizeof(double), cudaMemcpyHostToDevice, c->setup), "copy x");
   DGW_TRY(cudaMemcpyAsync(D_d, c->ref.D, sizeof(c->ref.D), cudaMemcpyHostToDevice, c->setup), "copy D");
@@ -430,11 +444,19 @@ dgw_status dgw_mesh_upload(dgw_ctx* c, int64_t nel, const double* x, const int64
   c->h_min = hmin;
   c->has_mesh = true;
   c->has_material = false;
+  if (c->cfg.system != DGW_SYSTEM_ELASTIC) {
+    // Q = I: no medium to upload; the wave speed is |beta| (transport) or sqrt(Phi) = 1.
+    const double* b = c->cfg.beta;
+    c->c_max = c->cfg.system == DGW_SYSTEM_TRANSPORT ? std::sqrt(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]) : 1.0;
+    c->has_material = true;
+  }
   return DGW_OK;
 }
 
 dgw_status dgw_material_upload(dgw_ctx* c, const double* rho, const double* lam, const double* mu) {
   if (!c) return fail(nullptr, DGW_ERR_ARG, "null context");
+  if (c->cfg.system != DGW_SYSTEM_ELASTIC)
+    return fail(c, DGW_ERR_UNSUPPORTED, "transport and shallow water have no medium (Q = I)");
   if (!c->has_mesh) return fail(c, DGW_ERR_STATE, "material before mesh");
   if (!rho || !lam || !mu) return fail(c, DGW_ERR_ARG, "null material array");
   const long long nel = c->nel;
@@ -498,7 +520,7 @@ dgw_status dgw_material_upload(dgw_ctx* c, const double* rho, const double* lam,
 }
 
 static dgw_status ensure_staging(dgw_ctx* c, bool need_res) {
-  const size_t bytes = (size_t)c->nel * Np_of(c->cfg.N) * 9 * sizeof(double);
+  const size_t bytes = (size_t)c->nel * Np_of(c->cfg.N) * c->m * sizeof(double);
   if (!c->stage_u) DGW_CUDA(c, cudaMalloc(&c->stage_u, bytes), "alloc staging state");
   if (need_res && !c->stage_res) DGW_CUDA(c, cudaMalloc(&c->stage_res, bytes), "alloc staging register");
   return DGW_OK;
@@ -510,7 +532,7 @@ dgw_status dgw_rhs(dgw_ctx* c, const double* u, double* rhs, double t, void* str
   if (!u || !rhs || (const void*)u == (void*)rhs) return fail(c, DGW_ERR_ARG, "u and rhs must be distinct non-null buffers");
   if (set_device(c) != DGW_OK) return DGW_ERR_CUDA;
   cudaStream_t s = (cudaStream_t)stream;
-  const size_t bytes = (size_t)c->nel * Np_of(c->cfg.N) * 9 * sizeof(double);
+  const size_t bytes = (size_t)c->nel * Np_of(c->cfg.N) * c->m * sizeof(double);
   const bool host = !is_device_ptr(u) || !is_device_ptr(rhs);
   if (!host) return launch_stage(c, u, rhs, nullptr, false, 0.0, 0.0, 0.0, s, nullptr, t);
   if ((st = ensure_staging(c, true)) != DGW_OK) return st;
@@ -553,7 +575,7 @@ dgw_status dgw_stage_energy(dgw_ctx* c, const double* u_in, double* u_out, doubl
                         t + kLsrkC[stage] * dt)) != DGW_OK)
     return st;
   double* result = c->stage_partials + c->stage_ctas;
-  DGW_CUDA(c, dgw::launch_energy_final(c->stage_partials, c->stage_ctas, result, s), "energy reduction");
+  DGW_CUDA(c, dgw::launch_energy_final(c->stage_partials, c->stage_ctas, result + 1, result, s), "energy reduction");
   double value = 0.0;
   DGW_CUDA(c, cudaMemcpyAsync(&value, result, sizeof(double), cudaMemcpyDeviceToHost, s), "copy energy");
   DGW_CUDA(c, cudaStreamSynchronize(s), "stage energy");
@@ -570,7 +592,7 @@ dgw_status dgw_step(dgw_ctx* c, double* u, double* res, double t0, double dt, in
   if (!std::isfinite(dt)) return fail(c, DGW_ERR_ARG, "dt must be finite");
   if (set_device(c) != DGW_OK) return DGW_ERR_CUDA;
   cudaStream_t s = (cudaStream_t)stream;
-  const size_t bytes = (size_t)c->nel * Np_of(c->cfg.N) * 9 * sizeof(double);
+  const size_t bytes = (size_t)c->nel * Np_of(c->cfg.N) * c->m * sizeof(double);
   const bool host = !is_device_ptr(u) || !is_device_ptr(res);
   double* ud = u;
   double* rd = res;
@@ -612,12 +634,18 @@ dgw_status dgw_energy(dgw_ctx* c, const double* u, double* energy_out, void* str
   const double* ud = u;
   if (!is_device_ptr(u)) {
     if ((st = ensure_staging(c, false)) != DGW_OK) return st;
-    const size_t bytes = (size_t)c->nel * Np_of(c->cfg.N) * 9 * sizeof(double);
+    const size_t bytes = (size_t)c->nel * Np_of(c->cfg.N) * c->m * sizeof(double);
     DGW_CUDA(c, cudaMemcpyAsync(c->stage_u, u, bytes, cudaMemcpyDefault, s), "copy u in");
     ud = c->stage_u;
   }
   double* result = c->partials + dgw::kEnergyBlocks;
-  DGW_CUDA(c, dgw::launch_energy(ud, c->wJ, c->ec, c->nel, Np_of(c->cfg.N), c->partials, result, s), "energy kernels");
+  if (c->cfg.system == DGW_SYSTEM_ELASTIC) {
+    DGW_CUDA(c, dgw::launch_energy(ud, c->wJ, c->ec, c->nel, Np_of(c->cfg.N), c->partials, result, s),
+             "energy kernels");
+  } else {
+    DGW_CUDA(c, dgw::launch_plain_energy(ud, c->wJ, c->m, c->nel * Np_of(c->cfg.N), c->partials, result, s),
+             "energy kernels");
+  }
   double value = 0.0;
   DGW_CUDA(c, cudaMemcpyAsync(&value, result, sizeof(double), cudaMemcpyDeviceToHost, s), "copy energy");
   DGW_CUDA(c, cudaStreamSynchronize(s), "energy");
@@ -629,6 +657,7 @@ dgw_status dgw_energy(dgw_ctx* c, const double* u, double* energy_out, void* str
 dgw_status dgw_source_set(dgw_ctx* c, int64_t element, const double* xi, const double* force, double f0,
                           double t0) {
   if (!c) return fail(nullptr, DGW_ERR_ARG, "null context");
+  if (c->cfg.system != DGW_SYSTEM_ELASTIC) return fail(c, DGW_ERR_UNSUPPORTED, "point forces are elastic only");
   if (!c->has_mesh || !c->has_material) return fail(c, DGW_ERR_STATE, "source before mesh and material");
   if (element < 0) {
     dfree(c->src_w);

@@ -58,6 +58,18 @@ energy_final_kernel(const double* __restrict__ partials, int nparts, double* res
   if (threadIdx.x == 0) *result = 0.5 * s;
 }
 
+// Block b sums partials[b * chunk, min((b + 1) * chunk, n)) into out[b].
+__global__ void __launch_bounds__(kEnergyThreads)
+energy_chunk_kernel(const double* __restrict__ partials, int nparts, int chunk, double* out) {
+  __shared__ double red[32];
+  const long long lo = static_cast<long long>(blockIdx.x) * chunk;
+  const long long hi = lo + chunk < nparts ? lo + chunk : nparts;
+  double acc = 0.0;
+  for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) acc += partials[i];
+  const double v = block_sum(acc, red);
+  if (threadIdx.x == 0) out[blockIdx.x] = v;
+}
+
 }  // namespace
 
 cudaError_t launch_energy(const double* u, const double* wJ, const double* ec, long long nel, int Np,
@@ -78,8 +90,20 @@ cudaError_t launch_energy(const double* u, const double* wJ, const double* ec, l
   return cudaGetLastError();
 }
 
-cudaError_t launch_energy_final(const double* partials, int nparts, double* result, cudaStream_t s) {
-  energy_final_kernel<<<1, kEnergyThreads, 0, s>>>(partials, nparts, result);
+cudaError_t launch_energy_final(const double* partials, int nparts, double* scratch, double* result,
+                                cudaStream_t s) {
+  if (nparts <= 8 * kEnergyThreads) {
+    energy_final_kernel<<<1, kEnergyThreads, 0, s>>>(partials, nparts, result);
+    return cudaGetLastError();
+  }
+  // Two levels: contiguous chunks per block, then one block over the chunk sums
+  // (fixed grid for a given nparts, so the order of the sum is fixed too).
+  const int chunk = (nparts + kEnergyBlocks - 1) / kEnergyBlocks;
+  const int blocks = (nparts + chunk - 1) / chunk;
+  energy_chunk_kernel<<<blocks, kEnergyThreads, 0, s>>>(partials, nparts, chunk, scratch);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  energy_final_kernel<<<1, kEnergyThreads, 0, s>>>(scratch, blocks, result);
   return cudaGetLastError();
 }
 

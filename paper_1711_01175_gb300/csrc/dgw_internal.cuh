@@ -68,6 +68,7 @@ struct StageParams {
   // that the FP32 path reads them from the constant bank without conversions.
   float dt_f, tau_f, hlift_f;
   int first;
+  double beta[3];           // transport velocity (generic-system kernel only)
   double D[(kMaxN + 1) * (kMaxN + 1)];
 };
 
@@ -144,7 +145,15 @@ constexpr int kEnergyBlocks = 152 * 4;
 constexpr int kEnergyThreads = 256;
 cudaError_t launch_energy(const double* u, const double* wJ, const double* ec, long long nel, int Np,
                           double* partials, double* result, cudaStream_t s);
-cudaError_t launch_energy_final(const double* partials, int nparts, double* result, cudaStream_t s);
+// Generic Friedrichs systems (dgw_friedrichs.cu): stage launch (FP64) and the
+// energy 1/2 sum w J |u|^2 of an m-field state (partials: kEnergyBlocks doubles).
+cudaError_t launch_friedrichs(int system, int N, bool lsrk, const StageParams& p, cudaStream_t s);
+cudaError_t launch_plain_energy(const double* u, const double* wJ, int m, long long total, double* partials,
+                                double* result, cudaStream_t s);
+
+// Sum nparts partials into *result (x 1/2); scratch holds kEnergyBlocks doubles.
+cudaError_t launch_energy_final(const double* partials, int nparts, double* scratch, double* result,
+                                cudaStream_t s);
 
 // Message storage of calls without a context (read by dgw_last_error(NULL)).
 void set_no_context_error(const std::string& msg);
@@ -156,6 +165,7 @@ struct dgw_ctx {
   int sm_count = 0;
   cudaStream_t setup = nullptr;    // private non-blocking stream for uploads and geometry
   dgw_config cfg{};
+  int m = 9;                       // fields of the system (9 elastic, 1 transport, 3 shallow water)
   dgw::RefElem ref;
   long long nel = 0;
   bool has_mesh = false;
@@ -169,7 +179,7 @@ struct dgw_ctx {
   double* wJ = nullptr;      // [nel][Np]
   double* u2 = nullptr;      // second state buffer for the stage ping-pong
   double* partials = nullptr;  // energy partial sums + result slot
-  double* stage_partials = nullptr;  // per-CTA energy partials of a fused stage + result slot
+  double* stage_partials = nullptr;  // per-CTA energy partials of a fused stage, result slot, reduction scratch
   int stage_ctas = 0;
   double* stage_u = nullptr;   // host-pointer staging buffers
   double* stage_res = nullptr;

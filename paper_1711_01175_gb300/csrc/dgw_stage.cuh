@@ -83,12 +83,15 @@ __device__ __forceinline__ float narrow_int(double d) {
 }
 
 __device__ __forceinline__ double widen_int(float x) {
+  // exponent + 896 and mantissa << 29 on the two 32-bit halves
   const unsigned u = __float_as_uint(x);
-  const unsigned e = (u >> 23) & 0xffu;
-  const unsigned long long sign = static_cast<unsigned long long>(u & 0x80000000u) << 32;
-  unsigned long long mag = static_cast<unsigned long long>(u & 0x7fffffffu) << 29;
-  mag = (e == 255u) ? (mag | 0x7ff0000000000000ull) : (mag + (896ull << 52));
-  return __longlong_as_double(static_cast<long long>(e == 0u ? sign : (sign | mag)));
+  const unsigned a = u & 0x7fffffffu;
+  const unsigned e = a >> 23;
+  unsigned hi = (a >> 3) + (e == 255u ? (1792u << 20) : (896u << 20));
+  unsigned lo = u << 29;
+  hi = e == 0u ? 0u : hi;
+  lo = e == 0u ? 0u : lo;
+  return __hiloint2double(static_cast<int>(hi | (u & 0x80000000u)), static_cast<int>(lo));
 }
 
 // A scalar parameter in the path's precision: the double, or its FP32 copy.

@@ -1,6 +1,7 @@
 """Tensor-level front end over the C ABI: one ``Solver`` per mesh and medium.
 
-Field tensors are ``[9, nel, Np]`` float64, either CUDA tensors (device
+Field tensors are ``[m, nel, Np]`` float64 (m = 9 for elasticity, 1 for
+transport, 3 for shallow water), either CUDA tensors (device
 pointers; the work is enqueued on torch's current stream) or CPU tensors /
 numpy arrays (host pointers; the library stages them through its own device
 buffers).  PyTorch only provides device memory and streams here.
@@ -42,14 +43,24 @@ def reference_nodes(N: int):
     return r, w
 
 
-class Solver:
-    """A DG elastic-wave operator on one mesh/medium (owns a dgw_ctx)."""
+SYSTEMS = {"elastic": (capi.DGW_SYSTEM_ELASTIC, 9), "transport": (capi.DGW_SYSTEM_TRANSPORT, 1),
+           "shallow_water": (capi.DGW_SYSTEM_SHALLOW_WATER, 3)}
 
-    def __init__(self, N: int, tau: int = 1, precision: str = "fp64", cfl: float = 0.5, device: int = 0):
+
+class Solver:
+    """A DG operator on one mesh (and, for elasticity, one medium); owns a dgw_ctx.
+
+    system: "elastic" (default), "transport" (velocity ``beta``) or
+    "shallow_water" (Phi = 1); the last two take no medium and run in FP64."""
+
+    def __init__(self, N: int, tau: int = 1, precision: str = "fp64", cfl: float = 0.5, device: int = 0,
+                 system: str = "elastic", beta=(0.0, 0.0, 0.0)):
         prec = {"fp64": capi.DGW_PRECISION_FP64, "mixed": capi.DGW_PRECISION_MIXED}[precision]
+        sys_id, self.m = SYSTEMS[system]
+        self.system = system
         self.N, self.tau, self.precision = int(N), int(tau), precision
         self.Np = (self.N + 1) ** 3
-        cfg = capi.dgw_config(self.N, self.tau, prec, float(cfl))
+        cfg = capi.dgw_config(self.N, self.tau, prec, float(cfl), sys_id, (ctypes.c_double * 3)(*[float(b) for b in beta]))
         st, h = capi.dgw_create(int(device), cfg)
         capi.check(st)
         self._ctx = h
@@ -96,8 +107,8 @@ class Solver:
         if self.nel == 0:
             return          # no mesh yet: the C ABI reports the call-order error
         shape = tuple(a.shape)
-        if shape != (9, self.nel, self.Np):
-            raise ValueError(f"{name} must be [9, {self.nel}, {self.Np}], got {shape}")
+        if shape != (self.m, self.nel, self.Np):
+            raise ValueError(f"{name} must be [{self.m}, {self.nel}, {self.Np}], got {shape}")
         if str(a.dtype) not in ("float64", "torch.float64"):
             raise ValueError(f"{name} must be float64")
 

@@ -74,6 +74,30 @@ def test_create_rejects_bad_config_without_touching_a_device(lib):
         assert st == -1 and not h.value
 
 
+def test_create_rejects_bad_system_config_without_touching_a_device(lib):
+    from paper_1711_01175_gb300 import capi
+    B = ctypes.c_double * 3
+    bad = [(capi.dgw_config(3, 1, 0, 0.5, 7, B(0, 0, 0)), -1),                    # unknown system
+           (capi.dgw_config(3, 1, 0, 0.5, capi.DGW_SYSTEM_TRANSPORT, B(0, 0, 0)), -1),   # beta = 0
+           (capi.dgw_config(3, 1, 1, 0.5, capi.DGW_SYSTEM_SHALLOW_WATER, B(0, 0, 0)), -7),  # mixed: not built
+           (capi.dgw_config(3, 1, 1, 0.5, capi.DGW_SYSTEM_TRANSPORT, B(1, 0, 0)), -7)]
+    for cfg, want in bad:
+        st, h = capi.dgw_create(0, cfg)
+        assert st == want and not h.value, capi.dgw_last_error(None)
+
+
+def test_config_struct_layout_matches_the_header():
+    """dgw_config as the C compiler lays it out: int N, flux_tau, precision;
+    double cfl; int system; double beta[3]."""
+    from paper_1711_01175_gb300 import capi
+    text = open(os.path.join(ROOT, "include", "dgw.h")).read()
+    body = re.search(r"typedef struct \{(.*?)\} dgw_config;", text, re.S).group(1)
+    names = re.findall(r"^\s*(?:int|double)\s+(\w+)", body, re.M)
+    assert names == [f[0] for f in capi.dgw_config._fields_] == ["N", "flux_tau", "precision", "cfl", "system", "beta"]
+    assert ctypes.sizeof(capi.dgw_config) == 56
+    assert capi.dgw_config.beta.offset == 32
+
+
 def test_calls_on_null_context_fail_cleanly(lib):
     from paper_1711_01175_gb300 import capi
     assert capi.dgw_rhs(None, None, None, 0.0, None) == -1

@@ -1,0 +1,165 @@
+"""Generic Friedrichs systems on the GPU (transport, linearized shallow water)
+against the oracle's FriedrichsDG, through the C ABI.
+
+* right-hand side: every degree's tile shape (ragged tiles, rotated warped
+  elements), central and upwind flux: <= 1e-12 relative L2;
+* each fused LSRK stage, a full step and the energies (separate and fused):
+  <= 1e-12;
+* the whole path at larger sizes against the paper's exact standing wave
+  (Section 6.3): design-order convergence of the GPU result;
+* elastic-only calls and undefined boundary tags are refused.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+from harness import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+BETA = (0.2, 0.3, -0.1)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__ as g
+    g.build()
+
+
+class FCase:
+    def __init__(self, system, E, N, amplitude=0.08, tau=1, rotate=None, seed=0):
+        from paper_1711_01175_gb300 import Solver, reference_nodes
+        if system == "transport":
+            mesh = wl.structured_hex_mesh(E)
+            sysm = oracle.transport(BETA)
+        else:
+            mesh = wl.structured_hex_mesh(E, (False, False, True),
+                                          {0: wl.BC_WALL, 1: wl.BC_WALL, 2: wl.BC_WALL, 3: wl.BC_ABSORBING})
+            sysm = oracle.shallow_water()
+        if rotate is not None:
+            mesh = wl.rotate_elements(mesh, rotate)
+        self.mesh, self.N, self.m = mesh, N, sysm.m
+        r_lib, _ = reference_nodes(N)
+        r_or, _ = oracle.gll(N)
+        self.x_lib = wl.warped_node_coords(mesh, r_lib, amplitude)
+        self.x_or = wl.warped_node_coords(mesh, r_or, amplitude)
+        self.solver = Solver(N, tau=tau, system=system, beta=BETA)
+        self.solver.upload_mesh(self.x_lib, mesh.etoe, mesh.etof, mesh.orient, mesh.bc)
+        self.op = oracle.FriedrichsDG(N, self.x_or, mesh.etoe, mesh.etof, mesh.orient, mesh.bc, sysm, tau)
+        self.u0 = wl.random_fields(self.m, mesh.nel, (N + 1) ** 3, seed)
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("system,N,E", [("transport", 1, 3), ("transport", 3, 3), ("transport", 4, 2),
+                                        ("transport", 7, 2), ("shallow_water", 2, (4, 3, 1)),
+                                        ("shallow_water", 3, (3, 3, 2)), ("shallow_water", 4, (3, 2, 1)),
+                                        ("shallow_water", 7, (2, 2, 1))])
+@pytest.mark.parametrize("tau", [0, 1])
+def test_rhs_parity(system, N, E, tau):
+    import torch
+    c = FCase(system, E, N, tau=tau, rotate=11, seed=N)
+    u = _dev(c.u0)
+    out = torch.empty_like(u)
+    c.solver.rhs(u, out)
+    assert rel_l2(out.cpu().numpy(), c.op.rhs(c.u0)) < TOL
+
+
+@pytest.mark.parametrize("system,E", [("transport", 3), ("shallow_water", (4, 3, 1))])
+def test_stages_step_and_energy_parity(system, E):
+    import torch
+    from paper_1711_01175_gb300 import capi
+    c = FCase(system, E, 3, rotate=5, seed=2)
+    dt = c.solver.dt_cfl()
+    assert np.isclose(dt, oracle.cfl_dt(0.5, oracle.h_min_corner_edges(c.x_or, 3), c.op.c_max(), 3), rtol=1e-12)
+    u_in = _dev(c.u0)
+    u_out = torch.empty_like(u_in)
+    res = torch.zeros_like(u_in)
+    uo, ro = c.u0.copy(), np.zeros_like(c.u0)
+    stream = torch.cuda.current_stream().cuda_stream
+    for s in range(5):
+        if s < 4:
+            assert capi.dgw_stage(c.solver._ctx, u_in.data_ptr(), u_out.data_ptr(), res.data_ptr(), s, 0.0, dt,
+                                  stream) == 0
+        else:
+            st, e_fused = capi.dgw_stage_energy(c.solver._ctx, u_in.data_ptr(), u_out.data_ptr(), res.data_ptr(),
+                                                s, 0.0, dt, stream)
+            assert st == 0
+        uo, ro = c.op.lsrk_stage(uo, ro, s, dt)
+        assert rel_l2(u_out.cpu().numpy(), uo) < TOL
+        assert rel_l2(res.cpu().numpy(), ro) < TOL
+        u_in, u_out = u_out, u_in
+    E_ref = c.op.energy(uo)
+    assert abs(e_fused - E_ref) <= TOL * E_ref
+    assert abs(c.solver.energy(u_in) - E_ref) <= TOL * E_ref
+    # dgw_step over two steps from the initial state
+    u = _dev(c.u0)
+    r = torch.zeros_like(u)
+    c.solver.step(u, r, dt, 2)
+    u2, r2 = c.u0.copy(), np.zeros_like(c.u0)
+    for k in range(2):
+        u2, r2 = c.op.step(u2, r2, dt, t=k * dt)
+    assert rel_l2(u.cpu().numpy(), u2) < TOL
+
+
+def test_standing_wave_converges_at_design_order_on_the_gpu():
+    """The paper's shallow-water standing wave with walls (Section 6.3), N = 3,
+    run on the GPU to T = 0.25 on 4 x 4 and 16 x 16 meshes (the oracle's pin
+    covers 4 -> 8); the error against the exact solution falls at >= N + 1 - 0.4."""
+    import torch
+    from paper_1711_01175_gb300 import Solver, reference_nodes
+    N, T = 3, 0.25
+    errs = []
+    for E in (4, 16):
+        mesh = wl.structured_hex_mesh((E, E, 1), (False, False, True),
+                                      {0: wl.BC_WALL, 1: wl.BC_WALL, 2: wl.BC_WALL, 3: wl.BC_WALL})
+        x = wl.warped_node_coords(mesh, reference_nodes(N)[0], 0.0)
+        s = Solver(N, system="shallow_water")
+        s.upload_mesh(x, mesh.etoe, mesh.etof, mesh.orient, mesh.bc)
+        nsteps = int(np.ceil(T / s.dt_cfl()))
+        u = _dev(wl.shallow_water_standing_wave(x))
+        r = torch.zeros_like(u)
+        s.step(u, r, T / nsteps, nsteps)
+        d = u.cpu().numpy() - wl.shallow_water_standing_wave(x, T)
+        w = reference_nodes(N)[1]
+        wv = np.einsum("k,j,i->kji", w, w, w).ravel()
+        J = 1.0 / (8.0 * E * E)          # undeformed cells [0, 1/E]^2 x [0, 1]: J = (1/2E)(1/2E)(1/2)
+        errs.append(float(np.sqrt(np.sum(wv[None, None, :] * J * d * d))))
+    rate = np.log(errs[0] / errs[1]) / np.log(4.0)
+    assert rate > N + 1 - 0.4, (errs, rate)
+
+
+def test_refusals():
+    import torch
+    from paper_1711_01175_gb300 import Solver, capi, reference_nodes
+    mesh = wl.structured_hex_mesh(2, (True, True, False), {4: wl.BC_WALL, 5: wl.BC_ABSORBING})
+    x = wl.warped_node_coords(mesh, reference_nodes(2)[0], 0.0)
+    s = Solver(2, system="transport", beta=BETA)
+    with pytest.raises(capi.DGWError) as ei:
+        s.upload_mesh(x, mesh.etoe, mesh.etof, mesh.orient, mesh.bc)     # tag 1 is not a transport boundary
+    assert ei.value.status == -1
+    sw = Solver(2, system="shallow_water")
+    sw.upload_mesh(x, mesh.etoe, mesh.etof, mesh.orient, mesh.bc)
+    ones = np.ones(mesh.nel)
+    assert capi.dgw_material_upload(sw._ctx, ones.ctypes.data, ones.ctypes.data, ones.ctypes.data) == -7
+    xi = np.zeros(3)
+    assert capi.dgw_source_set(sw._ctx, 0, xi.ctypes.data, xi.ctypes.data, 1.0, 0.0) == -7
+    el = np.zeros(1, dtype=np.int64)
+    assert capi.dgw_receivers_set(sw._ctx, 1, el.ctypes.data, xi.ctypes.data) == -7
+    z = torch.zeros((3, mesh.nel, 27), dtype=torch.float64, device="cuda")
+    g = torch.zeros((3, mesh.nel), dtype=torch.float64, device="cuda")
+    assert capi.dgw_adjoint_step(sw._ctx, z.data_ptr(), z.clone().data_ptr(), g.data_ptr(), z.clone().data_ptr(),
+                                 0.0, 0.01, 1, None) == -7
+    st, hb = capi.dgw_batch_create(0, 2, 0, 1, 4)
+    assert st == 0
+    P, D = ctypes.c_void_p * 1, ctypes.c_double * 1
+    assert capi.dgw_batch_set(hb, 1, P(sw._ctx.value), P(z.data_ptr()), P(z.clone().data_ptr()), D(0.01), D(0.0),
+                              None) == -7
+    capi.dgw_batch_destroy(hb)
