@@ -1,0 +1,104 @@
+"""Plain FP64 CPU oracle for the iHDG-II iteration (the paper's Section 3 and
+Algorithm "The iHDG-II approach") on the upwind DG/HDG transport operator.
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+``bench.py`` (its CPU-baseline / reference leg) may import or run this module.
+
+The problem is  sigma u - L(u) = b  with L the semi-discrete transport
+operator of ``FriedrichsDG`` (upwind flux, trace eliminated) and b given:
+* sigma = 0, b = f: the steady transport equation (Section 3.1,
+  eq. transport) with forcing f;
+* sigma = 1/dt, b = u^m / dt + f: one implicit Euler step of the
+  time-dependent transport equation (Section 3.3, eq. implicitHDG), of which
+  iHDG-II is the locally implicit solver (Section 3.3).
+
+iHDG-II, iteration k -> k+1 (eqs. iHDGlocal and iHDGtrace): every element K
+solves its local problem with its own unknowns at k+1 and its neighbours'
+at k inside the weighted trace.  The operator is linear, so
+L(u)_K = L_K^self u_K + L_K^nbr(u) with L_K^self the map u_K -> L(u)_K when
+every other element is zero, and the local solve reads
+    (sigma I - L_K^self) u_K^{k+1} = b_K + L_K^nbr(u^k).
+Stopping: eq. tolerancecriteria when the exact solution is given, else
+eq. tolerancecriteriarelerror, with the L2 norm of the mass matrix.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def element_coloring(etoe):
+    """Greedy colouring of the element graph: elements sharing a face differ in colour."""
+    nel = etoe.shape[0]
+    color = -np.ones(nel, dtype=np.int64)
+    for e in range(nel):
+        used = {int(color[n]) for n in etoe[e] if n >= 0 and color[n] >= 0}
+        c = 0
+        while c in used:
+            c += 1
+        color[e] = c
+    return color
+
+
+class IHDGTransport:
+    def __init__(self, op, sigma):
+        """op: a FriedrichsDG of the transport system; sigma >= 0."""
+        if op.m != 1:
+            raise ValueError("iHDG-II oracle: scalar transport only")
+        self.op = op
+        self.sigma = float(sigma)
+        self.nel, self.Np = op.nel, op.Np
+        _, J = op.geometry(np.arange(op.nel))
+        self.wJ = op.w_vol[None, :] * J                      # [nel, Np] mass weights
+        # L_K^self for every element: with a colouring, elements of one colour
+        # do not touch, so a unit vector in node j of all of them gives column j
+        # of each one's self block.
+        color = element_coloring(op.etoe)
+        self.Lself = np.zeros((self.nel, self.Np, self.Np))
+        for c in range(int(color.max()) + 1):
+            sel = np.nonzero(color == c)[0]
+            for j in range(self.Np):
+                u = np.zeros((1, self.nel, self.Np))
+                u[0, sel, j] = 1.0
+                self.Lself[sel, :, j] = op.rhs(u)[0, sel]
+        self.local = self.sigma * np.eye(self.Np)[None] - self.Lself      # sigma I - L_K^self
+
+    def neighbour_term(self, u):
+        """L_K^nbr(u) = L(u)_K - L_K^self u_K for every element: [1, nel, Np]."""
+        return self.op.rhs(u) - np.einsum("eij,ej->ei", self.Lself, u[0])[None]
+
+    def iterate(self, b, u):
+        """One iHDG-II iteration from u^k: the local solves of every element."""
+        rhs = b + self.neighbour_term(u)
+        return np.linalg.solve(self.local, rhs[0][..., None])[..., 0][None]
+
+    def norm(self, d):
+        return float(np.sqrt(np.sum(self.wJ[None] * d * d)))
+
+    def solve(self, b, u0, tol=1e-10, max_iter=1000, exact=None):
+        """Iterate to the paper's stopping criterion; returns (u, iterations, history of
+        ||u^k - u^{k-1}||)."""
+        u = np.array(u0, dtype=np.float64)
+        hist = []
+        prev_err = None if exact is None else self.norm(u - exact)
+        for k in range(1, max_iter + 1):
+            un = self.iterate(b, u)
+            hist.append(self.norm(un - u))
+            u = un
+            if exact is not None:
+                err = self.norm(u - exact)
+                if abs(err - prev_err) < tol:
+                    return u, k, hist
+                prev_err = err
+            elif hist[-1] < tol:
+                return u, k, hist
+        return u, max_iter, hist
+
+    def direct(self, b):
+        """The fixed point by a direct solve of sigma u - L(u) = b (assembled by columns)."""
+        n = self.nel * self.Np
+        A = np.zeros((n, n))
+        for j in range(n):
+            e = np.zeros(n)
+            e[j] = 1.0
+            A[:, j] = self.sigma * e - self.op.rhs(e.reshape(1, self.nel, self.Np)).ravel()
+        return np.linalg.solve(A, b.ravel()).reshape(b.shape)

@@ -1,0 +1,110 @@
+"""Pins of the iHDG-II oracle (Section 3, Algorithm "The iHDG-II approach").
+
+* the local blocks: L_K^self from the colouring equals the element-by-element
+  definition, and L_K^self u_K + L_K^nbr(u) = L(u)_K;
+* a fixed point of the iteration solves sigma u - L(u) = b (direct solve);
+* finite convergence for upwind transport (Theorem DDMConvergence): with
+  beta > 0 componentwise on an E^3 structured mesh the iterate equals the
+  direct solution after exactly 3E - 2 iterations (one per diagonal layer of
+  elements, counted from the inflow corner), independent of the degree;
+* the iteration counts of the paper's table (golden fixture), with its
+  stopping criterion (eq. tolerancecriteria): within one iteration, and the
+  asymptotics d N_el^(1/d);
+* the locally implicit use (Section 3.3): one implicit Euler step solved by
+  iHDG-II equals the direct implicit step.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+from oracle.ihdg import IHDGTransport, element_coloring
+
+BETA = np.array([1.0, 0.7, 0.4])
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "ihdg_transport_iterations.txt")
+
+
+def _op(E, N, a=0.0, periodic=False, beta=BETA):
+    mesh = wl.structured_hex_mesh(E, (periodic,) * 3)
+    r, _ = oracle.gll(N)
+    x = wl.warped_node_coords(mesh, r, a)
+    return oracle.FriedrichsDG(N, x, mesh.etoe, mesh.etof, mesh.orient, mesh.bc, oracle.transport(beta)), x
+
+
+def _manufactured(x, beta=BETA):
+    """u^e = prod sin(pi x_i) (zero on every boundary face, so the zero exterior
+    state is the exact inflow data) and f = beta . grad u^e at the nodes."""
+    X = np.pi * x
+    s, c = np.sin(X), np.cos(X)
+    ue = np.prod(s, axis=-1)
+    grad = np.pi * np.stack([c[..., 0] * s[..., 1] * s[..., 2], s[..., 0] * c[..., 1] * s[..., 2],
+                             s[..., 0] * s[..., 1] * c[..., 2]], axis=-1)
+    return ue[None], (grad @ beta)[None]
+
+
+def test_self_blocks_and_splitting():
+    op, _ = _op(3, 2, a=0.05)
+    ih = IHDGTransport(op, 0.0)
+    color = element_coloring(op.etoe)
+    for e in range(op.nel):
+        assert all(color[n] != color[e] for n in op.etoe[e] if n >= 0)
+    K = 13
+    for j in (0, 5, 26):
+        u = np.zeros((1, op.nel, op.Np))
+        u[0, K, j] = 1.0
+        assert np.allclose(ih.Lself[K][:, j], op.rhs(u)[0, K], atol=1e-13)
+    u = wl.random_fields(1, op.nel, op.Np, 3)
+    lhs = np.einsum("eij,ej->ei", ih.Lself, u[0])[None] + ih.neighbour_term(u)
+    assert np.allclose(lhs, op.rhs(u), atol=1e-12)
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+def test_finite_convergence_after_one_iteration_per_layer(N):
+    E = 3
+    op, x = _op(E, N)
+    ih = IHDGTransport(op, 0.0)
+    _, f = _manufactured(x)
+    ud = ih.direct(f)
+    u = np.zeros_like(f)
+    for k in range(1, 3 * E - 2):
+        u = ih.iterate(f, u)
+        assert ih.norm(u - ud) > 1e-6 * ih.norm(ud), k
+    u = ih.iterate(f, u)                       # iteration 3E - 2
+    assert ih.norm(u - ud) < 1e-12 * ih.norm(ud)
+
+
+def _golden():
+    rows = [l.split() for l in open(GOLDEN) if l.strip() and not l.startswith("#")]
+    return {(int(E), int(p)): int(k) for E, p, k in rows}
+
+
+@pytest.mark.parametrize("E,N", [(2, 1), (4, 1), (8, 1), (2, 2), (4, 2), (2, 3), (2, 4)])
+def test_iteration_counts_of_the_paper(E, N):
+    op, x = _op(E, N)
+    ih = IHDGTransport(op, 0.0)
+    ue, f = _manufactured(x)
+    u, its, _ = ih.solve(f, np.zeros_like(f), tol=1e-10, exact=ue)
+    paper = _golden()[(E, N)]
+    assert its == 3 * E - 1                    # 3E - 2 layers, then one iteration without change
+    # The paper's counts are 3E - 1 from 8^3 on and one or two more on 2^3 and 4^3,
+    # where they also vary with p (6 or 7 on 2^3) although its theorem makes them
+    # p-independent; its velocity and exact solution are not printed.
+    assert abs(its - paper) <= (1 if E >= 4 else 2)
+    assert abs(its - 3 * E) <= 1               # d N_el^(1/d)
+    if op.nel * op.Np <= 2000:                 # the converged iterate is the HDG solution
+        ud = ih.direct(f)
+        assert ih.norm(u - ud) < 1e-10 * ih.norm(ud)
+
+
+def test_locally_implicit_step_equals_the_direct_implicit_step():
+    op, x = _op(3, 3, a=0.05, periodic=True, beta=np.array([0.2, 0.3, -0.1]))
+    dt = 2.0 * oracle.cfl_dt(1.0, 1.0 / 3, op.c_max(), 3)         # CFL 2
+    ih = IHDGTransport(op, 1.0 / dt)
+    um = wl.transport_periodic(x, (0.2, 0.3, -0.1))
+    b = um / dt
+    ud = ih.direct(b)
+    u, its, hist = ih.solve(b, um, tol=1e-12)
+    assert its < 40 and hist[-1] < 1e-12
+    assert ih.norm(u - ud) < 1e-10 * ih.norm(ud)
