@@ -276,6 +276,35 @@ const char* dgw_batch_last_error(const dgw_batch* b);
 dgw_status dgw_energy_static(int N, int64_t nel, const double* x, const double* u, const double* rho,
                              const double* lam, const double* mu, double* energy_out, void* stream);
 
+/* ---- iHDG-II: the paper's locally implicit iteration (transport) -------
+ * The paper's iHDG-II algorithm (Section 3, Algorithm "The iHDG-II
+ * approach"; eqs. iHDGlocal and iHDGtrace) for sigma u - L(u) = b with L the
+ * upwind transport operator of a DGW_SYSTEM_TRANSPORT context: every element
+ * solves its local problem with its own unknowns at iteration k+1 and its
+ * neighbours' at k in the weighted trace,
+ *     (sigma I - L_K^self) u_K^{k+1} = b_K + L_K^nbr(u^k).
+ * sigma = 0 is the steady transport equation (Section 3.1, forcing f);
+ * sigma = 1/dt with b = u^m/dt + f is one implicit Euler step solved
+ * element by element (Section 3.3, the locally implicit method).  N <= 4. */
+
+/* Build and invert sigma I - L_K^self for every element (device memory:
+ * nel * Np^2 doubles, about 1 MB per 8 elements at N = 4).  sigma >= 0.
+ * DGW_ERR_UNSUPPORTED unless the context is transport with N <= 4;
+ * DGW_ERR_STATE before the mesh; DGW_ERR_ARG if a local matrix is
+ * singular.  Synchronises `stream`. */
+dgw_status dgw_ihdg_setup(dgw_ctx* ctx, double sigma, void* stream);
+
+/* Iterate from the initial guess in u (device [nel][Np], overwritten with the
+ * result) with b = sigma * u_prev + f (device [nel][Np] each; either may be
+ * NULL for zero; neither may alias u) until ||u^k - u^{k-1}||_{L2} < tol (the
+ * paper's eq. tolerancecriteriarelerror, L2 norm of the mass matrix) or
+ * max_iter iterations.  *iterations receives the iterations done and
+ * *last_change (may be NULL) the last ||u^k - u^{k-1}||.  Synchronises
+ * `stream` once per iteration (the stopping test).  DGW_ERR_STATE before
+ * dgw_ihdg_setup; DGW_ERR_UNSTABLE on a non-finite iterate. */
+dgw_status dgw_ihdg_solve(dgw_ctx* ctx, const double* u_prev, const double* f, double* u, double tol, int max_iter,
+                          int* iterations, double* last_change, void* stream);
+
 /* Message of the last failing call on ctx (or of the last failing call
  * without a context when ctx is NULL).  Never NULL; owned by the library. */
 const char* dgw_last_error(const dgw_ctx* ctx);

@@ -58,6 +58,8 @@ SIGNATURES = {
     "dgw_batch_run": (_I, [_P, _I, _P]),
     "dgw_batch_last_error": (ctypes.c_char_p, [_P]),
     "dgw_energy_static": (_I, [_I, _I64, _P, _P, _P, _P, _P, _P, _P]),
+    "dgw_ihdg_setup": (_I, [_P, _D, _P]),
+    "dgw_ihdg_solve": (_I, [_P, _P, _P, _P, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), _P]),
     "dgw_last_error": (ctypes.c_char_p, [_P]),
 }
 
@@ -195,6 +197,17 @@ def dgw_batch_last_error(b):
 
 def dgw_energy_static(N, nel, x, u, rho, lam, mu, energy_out, stream):
     return load().dgw_energy_static(N, nel, x, u, rho, lam, mu, energy_out, stream)
+
+
+def dgw_ihdg_setup(ctx, sigma, stream):
+    return load().dgw_ihdg_setup(ctx, sigma, stream)
+
+
+def dgw_ihdg_solve(ctx, u_prev, f, u, tol, max_iter, stream):
+    its = _I()
+    change = _D()
+    st = load().dgw_ihdg_solve(ctx, u_prev, f, u, tol, max_iter, ctypes.byref(its), ctypes.byref(change), stream)
+    return st, its.value, change.value
 
 
 def dgw_last_error(ctx):

@@ -76,6 +76,7 @@ void free_mesh(dgw_ctx* c) {
   c->adj_gface_bytes = 0;
   dfree(c->etoe_d);
   dfree(c->etof_d);
+  dgw::ihdg_release(c);
   c->has_mesh = c->has_material = false;
   c->nel = 0;
 }

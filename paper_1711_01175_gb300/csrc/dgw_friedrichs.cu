@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(Shape<N>::NT) friedrichs_stage_kernel(const St
     const int g = p.vmapP[static_cast<size_t>(ei) * 6 * nf + r];
     if (g >= 0) {
 #pragma unroll
-      for (int q = 0; q < M; ++q) du[q] = u_s[q * NTILE + sidx] - p.u_in[q * fstride + g];
+      for (int q = 0; q < M; ++q) du[q] = u_s[q * NTILE + sidx] - (p.self_only ? 0.0 : p.u_in[q * fstride + g]);
     } else if (g == kGhostFreeSurface) {
       // shallow-water wall: exterior (phi, q - 2 (q.n) n), jump (0, 2 (q.n) n) with n
       // the horizontal part of the normal (the mesh upload refuses this tag for transport)

@@ -1,0 +1,395 @@
+// iHDG-II for the transport system (the paper's Section 3, Algorithm "The
+// iHDG-II approach"): solve sigma u - L(u) = b by element-local solves,
+//     (sigma I - L_K^self) u_K^{k+1} = b_K + L_K^nbr(u^k),
+// where the weighted trace of eq. iHDGtrace takes the element's own unknowns
+// at k+1 and its neighbours' at k.  With the upwind flux the neighbour
+// coupling of a face node is c (u^+)^k with
+//     c = -(1/(w_0 J)) 1/2 (beta.m - tau |beta.m|),   m = n sJ outward,
+// non-zero on inflow faces only.
+//
+// Set-up (dgw_ihdg_setup): L_K^self column by column from the transport stage
+// kernel in its self-only mode (neighbour states zero) applied to the unit
+// vector of node j in every element; sigma I - L_K^self is inverted per
+// element by Gauss-Jordan elimination with partial pivoting in shared memory
+// (one CTA per element) and stored transposed, so that the matrix-vector
+// product of an iteration reads it coalesced.  Iteration (dgw_ihdg_solve): one
+// CTA per element gathers the neighbour terms, applies the inverse, writes
+// u^{k+1} and a partial sum of w J (u^{k+1} - u^k)^2; the host stops on the
+// paper's criterion ||u^k - u^{k-1}||_{L2} < tol (eq. tolerancecriteriarelerror).
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "dgw_internal.cuh"
+
+namespace dgw {
+namespace {
+
+constexpr int kIhdgMaxN = 4;   // the inverse of a degree-4 element (125 x 125) fills 122 KB of shared memory
+
+__global__ void unit_column_kernel(double* u, long long total, int Np, int j) {
+  for (long long g = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; g < total;
+       g += static_cast<long long>(gridDim.x) * blockDim.x)
+    u[g] = (g % Np) == j ? 1.0 : 0.0;
+}
+
+// A[e][i][j] = sigma delta_ij - col[e][i]  (row-major blocks)
+__global__ void scatter_column_kernel(const double* col, double* A, long long total, int Np, int j, double sigma) {
+  for (long long g = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; g < total;
+       g += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long e = g / Np;
+    const int i = static_cast<int>(g - e * Np);
+    A[(e * Np + i) * Np + j] = (i == j ? sigma : 0.0) - col[g];
+  }
+}
+
+// In-place Gauss-Jordan inversion of each n x n block of A (partial pivoting;
+// row exchanges recorded and undone as column exchanges at the end), written
+// back transposed.  A zero pivot sets *singular.
+__global__ void __launch_bounds__(256) gj_invert_kernel(double* A, int n, long long nel, int* singular) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* a = reinterpret_cast<double*>(smem_raw);          // [n][n]
+  double* fcol = a + n * n;                                  // [n]
+  int* perm = reinterpret_cast<int*>(fcol + n);              // [n]
+  __shared__ int piv_row;
+  __shared__ double pinv;
+  const long long e = blockIdx.x;
+  if (e >= nel) return;
+  double* Ae = A + static_cast<size_t>(e) * n * n;
+  const int t = threadIdx.x, NT = blockDim.x;
+  for (int q = t; q < n * n; q += NT) a[q] = Ae[q];
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    if (t < 32) {
+      // pivot: the largest |a[i][k]|, i >= k (lowest index on ties)
+      double best = -1.0;
+      int bi = k;
+      for (int i = k + t; i < n; i += 32) {
+        const double v = fabs(a[i * n + k]);
+        if (v > best) {
+          best = v;
+          bi = i;
+        }
+      }
+      for (int off = 16; off > 0; off >>= 1) {
+        const double ob = __shfl_down_sync(0xffffffffu, best, off);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+        if (ob > best || (ob == best && oi < bi)) {
+          best = ob;
+          bi = oi;
+        }
+      }
+      if (t == 0) {
+        piv_row = bi;
+        perm[k] = bi;
+        if (!(best > 0.0)) atomicExch(singular, 1);
+      }
+    }
+    __syncthreads();
+    const int p = piv_row;
+    if (p != k) {
+      for (int j = t; j < n; j += NT) {
+        const double tmp = a[k * n + j];
+        a[k * n + j] = a[p * n + j];
+        a[p * n + j] = tmp;
+      }
+    }
+    __syncthreads();
+    if (t == 0) pinv = 1.0 / a[k * n + k];
+    __syncthreads();
+    for (int j = t; j < n; j += NT) a[k * n + j] = (j == k ? 1.0 : a[k * n + j]) * pinv;
+    for (int i = t; i < n; i += NT) fcol[i] = i == k ? 0.0 : a[i * n + k];
+    __syncthreads();
+    for (int q = t; q < n * n; q += NT) {
+      const int i = q / n, j = q - (q / n) * n;
+      if (i != k) a[q] = (j == k ? 0.0 : a[q]) - fcol[i] * a[k * n + j];
+    }
+    __syncthreads();
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    const int p = perm[k];
+    if (p != k) {
+      for (int i = t; i < n; i += NT) {
+        const double tmp = a[i * n + k];
+        a[i * n + k] = a[i * n + p];
+        a[i * n + p] = tmp;
+      }
+    }
+    __syncthreads();
+  }
+  for (int q = t; q < n * n; q += NT) {
+    const int i = q / n, j = q - (q / n) * n;
+    Ae[j * n + i] = a[q];
+  }
+}
+
+// c of every face node of every element (zero on boundary faces and outflow faces).
+template <int N>
+__global__ void face_coef_kernel(const double* geo, const int* vmapP, long long nel, double beta0, double beta1,
+                                 double beta2, double tau, double w_end_inv, double* cf) {
+  constexpr int n = N + 1, Np = n * n * n, nf = n * n;
+  const long long total = nel * 6 * nf;
+  const size_t fstride = static_cast<size_t>(nel) * Np;
+  for (long long g = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; g < total;
+       g += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long e = g / (6 * nf);
+    const int r = static_cast<int>(g - e * 6 * nf);
+    double c = 0.0;
+    if (vmapP[g] >= 0) {
+      const int f = r / nf, pf = r - (r / nf) * nf, d = f >> 1;
+      const bool hi = (f & 1) != 0;
+      const int fa = pf % n, fb = pf / n, cd = hi ? N : 0;
+      const int c0 = d == 0 ? cd : fa;
+      const int c1 = d == 0 ? fa : (d == 1 ? cd : fb);
+      const int c2 = d == 2 ? cd : fb;
+      const size_t gi = static_cast<size_t>(e) * Np + c0 + n * (c1 + n * c2);
+      const double sgn = hi ? 1.0 : -1.0;
+      const double bm = sgn * (beta0 * geo[(3 * d + 0) * fstride + gi] + beta1 * geo[(3 * d + 1) * fstride + gi] +
+                               beta2 * geo[(3 * d + 2) * fstride + gi]);
+      c = -0.5 * w_end_inv * geo[9 * fstride + gi] * (bm - tau * fabs(bm));
+    }
+    cf[g] = c;
+  }
+}
+
+// One iHDG-II iteration: u_next_K = inv_K (sigma u_prev_K + f_K + sum_faces c u_k^+),
+// and part[e] = sum_i w J (u_next - u_k)^2 over the element.
+template <int N>
+__global__ void __launch_bounds__(((N + 1) * (N + 1) * (N + 1) + 31) / 32 * 32)
+    ihdg_iter_kernel(const double* __restrict__ invT, const double* __restrict__ cf, const int* __restrict__ vmapP,
+                     const double* __restrict__ wJ, const double* u_prev, const double* f, double sigma,
+                     const double* __restrict__ uk, double* __restrict__ unext, long long nel, double* part) {
+  constexpr int n = N + 1, Np = n * n * n, nf = n * n, NT = (Np + 31) / 32 * 32;
+  __shared__ double rhs_s[Np];
+  __shared__ double x_s[6 * nf];
+  __shared__ double red[32];
+  const long long e = blockIdx.x;
+  const int t = threadIdx.x;
+  for (int r = t; r < 6 * nf; r += NT) {
+    const size_t gr = static_cast<size_t>(e) * 6 * nf + r;
+    const int g = vmapP[gr];
+    x_s[r] = g >= 0 ? cf[gr] * uk[g] : 0.0;
+  }
+  __syncthreads();
+  double rhs = 0.0;
+  const size_t gi = static_cast<size_t>(e) * Np + t;
+  if (t < Np) {
+    rhs = (u_prev ? sigma * u_prev[gi] : 0.0) + (f ? f[gi] : 0.0);
+    const int ix = t % n, iy = (t / n) % n, iz = t / nf;
+    if (ix == 0) rhs += x_s[0 * nf + iy + n * iz];
+    if (ix == N) rhs += x_s[1 * nf + iy + n * iz];
+    if (iy == 0) rhs += x_s[2 * nf + ix + n * iz];
+    if (iy == N) rhs += x_s[3 * nf + ix + n * iz];
+    if (iz == 0) rhs += x_s[4 * nf + ix + n * iy];
+    if (iz == N) rhs += x_s[5 * nf + ix + n * iy];
+    rhs_s[t] = rhs;
+  }
+  __syncthreads();
+  double v = 0.0;
+  if (t < Np) {
+    const double* M = invT + static_cast<size_t>(e) * Np * Np + t;
+    double acc = 0.0;
+#pragma unroll 5
+    for (int j = 0; j < Np; ++j) acc = fma(M[static_cast<size_t>(j) * Np], rhs_s[j], acc);
+    unext[gi] = acc;
+    const double d = acc - uk[gi];
+    v = wJ[gi] * d * d;
+  }
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  if ((t & 31) == 0) red[t >> 5] = v;
+  __syncthreads();
+  if (t == 0) {
+    double s = 0.0;
+    for (int w = 0; w < NT / 32; ++w) s += red[w];
+    part[e] = s;
+  }
+}
+
+template <int N>
+cudaError_t launch_iter(const dgw_ctx* c, const double* u_prev, const double* f, const double* uk, double* unext,
+                        cudaStream_t s) {
+  constexpr int Np = (N + 1) * (N + 1) * (N + 1), NT = (Np + 31) / 32 * 32;
+  ihdg_iter_kernel<N><<<(unsigned)c->nel, NT, 0, s>>>(c->ihdg_inv, c->ihdg_cf, c->vmapP, c->wJ, u_prev, f,
+                                                       c->ihdg_sigma, uk, unext, c->nel, c->ihdg_part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_iter_any(const dgw_ctx* c, const double* u_prev, const double* f, const double* uk, double* unext,
+                            cudaStream_t s) {
+  switch (c->cfg.N) {
+    case 1: return launch_iter<1>(c, u_prev, f, uk, unext, s);
+    case 2: return launch_iter<2>(c, u_prev, f, uk, unext, s);
+    case 3: return launch_iter<3>(c, u_prev, f, uk, unext, s);
+    case 4: return launch_iter<4>(c, u_prev, f, uk, unext, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_face_coef(const dgw_ctx* c, cudaStream_t s) {
+  const double* geo = static_cast<const double*>(c->geo);
+  const double tau = c->cfg.flux_tau ? 1.0 : 0.0;
+  const double wi = 1.0 / c->ref.w[0];
+  const double* b = c->cfg.beta;
+  const int blocks = 4 * c->sm_count;
+  switch (c->cfg.N) {
+#define DGW_FC(NN)                                                                                          \
+  case NN:                                                                                                  \
+    face_coef_kernel<NN><<<blocks, 256, 0, s>>>(geo, c->vmapP, c->nel, b[0], b[1], b[2], tau, wi, c->ihdg_cf); \
+    break;
+    DGW_FC(1) DGW_FC(2) DGW_FC(3) DGW_FC(4)
+#undef DGW_FC
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+dgw_status ifail(dgw_ctx* c, dgw_status st, const std::string& msg) {
+  if (c)
+    c->err = msg;
+  else
+    set_no_context_error(msg);
+  return st;
+}
+
+bool dev_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void ihdg_free(dgw_ctx* c) {
+  if (c->ihdg_inv) cudaFree(c->ihdg_inv);
+  if (c->ihdg_cf) cudaFree(c->ihdg_cf);
+  if (c->ihdg_part) cudaFree(c->ihdg_part);
+  if (c->ihdg_u2) cudaFree(c->ihdg_u2);
+  c->ihdg_inv = c->ihdg_cf = c->ihdg_part = c->ihdg_u2 = nullptr;
+  c->ihdg_ready = false;
+}
+
+}  // namespace
+
+void ihdg_release(dgw_ctx* c) { ihdg_free(c); }
+
+}  // namespace dgw
+
+#define ICUDA(call, what)                                                                 \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) return dgw::ifail(c, DGW_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+extern "C" {
+
+dgw_status dgw_ihdg_setup(dgw_ctx* c, double sigma, void* stream) {
+  if (!c) return dgw::ifail(nullptr, DGW_ERR_ARG, "null context");
+  if (c->cfg.system != DGW_SYSTEM_TRANSPORT) return dgw::ifail(c, DGW_ERR_UNSUPPORTED, "iHDG-II is built for transport");
+  if (c->cfg.N > dgw::kIhdgMaxN) return dgw::ifail(c, DGW_ERR_UNSUPPORTED, "iHDG-II is built for N <= 4");
+  if (!c->has_mesh) return dgw::ifail(c, DGW_ERR_STATE, "iHDG-II set-up before the mesh");
+  if (!(sigma >= 0.0) || !std::isfinite(sigma)) return dgw::ifail(c, DGW_ERR_ARG, "sigma must be finite and >= 0");
+  if (cudaSetDevice(c->device) != cudaSuccess) return dgw::ifail(c, DGW_ERR_CUDA, "cudaSetDevice");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int N = c->cfg.N, n = N + 1, Np = n * n * n, nf = n * n;
+  const long long nel = c->nel;
+  const size_t nodes = static_cast<size_t>(nel) * Np;
+  dgw::ihdg_free(c);
+  if (cudaMalloc(&c->ihdg_inv, nodes * Np * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&c->ihdg_cf, static_cast<size_t>(nel) * 6 * nf * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&c->ihdg_part, (static_cast<size_t>(nel) + 1 + dgw::kEnergyBlocks) * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&c->ihdg_u2, nodes * sizeof(double)) != cudaSuccess) {
+    dgw::ihdg_free(c);
+    return dgw::ifail(c, DGW_ERR_OOM, "iHDG-II buffers (" + std::to_string(nodes * Np * 8 / (1 << 20)) + " MB of inverses)");
+  }
+  int* singular = nullptr;
+  ICUDA(cudaMalloc(&singular, sizeof(int)), "alloc flag");
+  ICUDA(cudaMemsetAsync(singular, 0, sizeof(int), s), "clear flag");
+  // Columns of L_K^self: unit vector of node j in every element -> self-only operator.
+  dgw::StageParams p{};
+  p.u_in = c->ihdg_u2;
+  p.out = c->u2;
+  p.geo = c->geo;
+  p.vmapP = c->vmapP;
+  p.nel = nel;
+  p.tau = c->cfg.flux_tau ? 1.0 : 0.0;
+  p.w_end_inv = 1.0 / c->ref.w[0];
+  p.src_elem = -1;
+  p.self_only = 1;
+  for (int k = 0; k < 3; ++k) p.beta[k] = c->cfg.beta[k];
+  for (int i = 0; i < n * n; ++i) p.D[i] = c->ref.D[i];
+  const int blocks = 4 * c->sm_count;
+  cudaError_t e = cudaSuccess;
+  for (int j = 0; j < Np && e == cudaSuccess; ++j) {
+    dgw::unit_column_kernel<<<blocks, 256, 0, s>>>(c->ihdg_u2, static_cast<long long>(nodes), Np, j);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = dgw::launch_friedrichs(DGW_SYSTEM_TRANSPORT, N, false, p, s);
+    if (e == cudaSuccess) {
+      dgw::scatter_column_kernel<<<blocks, 256, 0, s>>>(c->u2, c->ihdg_inv, static_cast<long long>(nodes), Np, j, sigma);
+      e = cudaGetLastError();
+    }
+  }
+  if (e != cudaSuccess) {
+    cudaFree(singular);
+    return dgw::ifail(c, DGW_ERR_CUDA, std::string("local matrices: ") + cudaGetErrorString(e));
+  }
+  const size_t smem = static_cast<size_t>(Np) * Np * 8 + Np * 8 + Np * 4;
+  e = cudaFuncSetAttribute(dgw::gj_invert_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) {
+    dgw::gj_invert_kernel<<<(unsigned)nel, 256, smem, s>>>(c->ihdg_inv, Np, nel, singular);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = dgw::launch_face_coef(c, s);
+  int sing = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&sing, singular, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(singular);
+  if (e != cudaSuccess) return dgw::ifail(c, DGW_ERR_CUDA, std::string("local inverses: ") + cudaGetErrorString(e));
+  if (sing) {
+    dgw::ihdg_free(c);
+    return dgw::ifail(c, DGW_ERR_ARG, "a local matrix sigma I - L_K^self is singular");
+  }
+  c->ihdg_sigma = sigma;
+  c->ihdg_ready = true;
+  return DGW_OK;
+}
+
+dgw_status dgw_ihdg_solve(dgw_ctx* c, const double* u_prev, const double* f, double* u, double tol, int max_iter,
+                          int* iterations, double* last_change, void* stream) {
+  if (!c) return dgw::ifail(nullptr, DGW_ERR_ARG, "null context");
+  if (!c->ihdg_ready) return dgw::ifail(c, DGW_ERR_STATE, "dgw_ihdg_setup first");
+  if (!u || !iterations || max_iter < 1 || !(tol >= 0.0)) return dgw::ifail(c, DGW_ERR_ARG, "bad arguments");
+  if (!dgw::dev_ptr(u) || (u_prev && !dgw::dev_ptr(u_prev)) || (f && !dgw::dev_ptr(f)))
+    return dgw::ifail(c, DGW_ERR_ARG, "u, u_prev and f must be device buffers");
+  if (u_prev == u || f == u) return dgw::ifail(c, DGW_ERR_ARG, "u must not alias u_prev or f");
+  if (cudaSetDevice(c->device) != cudaSuccess) return dgw::ifail(c, DGW_ERR_CUDA, "cudaSetDevice");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = static_cast<size_t>(c->nel) * (c->cfg.N + 1) * (c->cfg.N + 1) * (c->cfg.N + 1) * sizeof(double);
+  double* cur = u;
+  double* nxt = c->ihdg_u2;
+  double* result = c->ihdg_part + c->nel;
+  double change = INFINITY;
+  int k = 0;
+  while (k < max_iter) {
+    ICUDA(dgw::launch_iter_any(c, u_prev, f, cur, nxt, s), "iteration kernel");
+    ICUDA(dgw::launch_energy_final(c->ihdg_part, static_cast<int>(c->nel), result + 1, result, s), "change norm");
+    double half_sq = 0.0;
+    ICUDA(cudaMemcpyAsync(&half_sq, result, sizeof(double), cudaMemcpyDeviceToHost, s), "copy change");
+    ICUDA(cudaStreamSynchronize(s), "iteration");
+    ++k;
+    double* tmp = cur;
+    cur = nxt;
+    nxt = tmp;
+    change = std::sqrt(2.0 * half_sq);           // the reduction returns half the sum
+    if (!std::isfinite(change)) return dgw::ifail(c, DGW_ERR_UNSTABLE, "iHDG-II iterate is not finite");
+    if (change < tol) break;
+  }
+  if (cur != u) ICUDA(cudaMemcpyAsync(u, cur, bytes, cudaMemcpyDeviceToDevice, s), "copy result");
+  ICUDA(cudaStreamSynchronize(s), "result");
+  *iterations = k;
+  if (last_change) *last_change = change;
+  return DGW_OK;
+}
+
+}  // extern "C"

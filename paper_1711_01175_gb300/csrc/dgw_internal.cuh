@@ -69,6 +69,7 @@ struct StageParams {
   float dt_f, tau_f, hlift_f;
   int first;
   double beta[3];           // transport velocity (generic-system kernel only)
+  int self_only;            // generic-system kernel: neighbour states taken as zero (L_K^self)
   double D[(kMaxN + 1) * (kMaxN + 1)];
 };
 
@@ -151,6 +152,9 @@ cudaError_t launch_friedrichs(int system, int N, bool lsrk, const StageParams& p
 cudaError_t launch_plain_energy(const double* u, const double* wJ, int m, long long total, double* partials,
                                 double* result, cudaStream_t s);
 
+// Free the iHDG-II buffers of a context (dgw_ihdg.cu).
+void ihdg_release(dgw_ctx* c);
+
 // Sum nparts partials into *result (x 1/2); scratch holds kEnergyBlocks doubles.
 cudaError_t launch_energy_final(const double* partials, int nparts, double* scratch, double* result,
                                 cudaStream_t s);
@@ -201,5 +205,13 @@ struct dgw_ctx {
   signed char* etof_d = nullptr;
   double h_min = 0.0;
   double c_max = 0.0;
+  // iHDG-II (transport): inverses of sigma I - L_K^self, transposed, and the
+  // neighbour-coupling coefficient of every face node
+  double* ihdg_inv = nullptr;        // [nel][Np][Np], entry (e, j, i) = inverse(e)[i][j]
+  double* ihdg_cf = nullptr;         // [nel][6*nf]
+  double* ihdg_part = nullptr;       // per-element partial sums + result + scratch
+  double* ihdg_u2 = nullptr;         // second iterate buffer [nel][Np]
+  double ihdg_sigma = 0.0;
+  bool ihdg_ready = false;
   std::string err;
 };

@@ -153,6 +153,23 @@ class Solver:
         self._check(st)
         return val
 
+    def ihdg_setup(self, sigma: float, stream=None):
+        """iHDG-II (transport, N <= 4): build and invert sigma I - L_K^self per element."""
+        self._check(capi.dgw_ihdg_setup(self._ctx, float(sigma), _stream_handle(stream)))
+
+    def ihdg_solve(self, u, u_prev=None, f=None, tol: float = 1e-10, max_iter: int = 1000, stream=None):
+        """Iterate iHDG-II from the guess in u (device [1, nel, Np], overwritten) for
+        sigma u - L(u) = sigma u_prev + f; returns (iterations, last ||u^k - u^{k-1}||)."""
+        self._field_check(u, "u")
+        for a, name in ((u_prev, "u_prev"), (f, "f")):
+            if a is not None:
+                self._field_check(a, name)
+        st, its, change = capi.dgw_ihdg_solve(self._ctx, None if u_prev is None else _ptr(u_prev),
+                                              None if f is None else _ptr(f), _ptr(u), float(tol), int(max_iter),
+                                              _stream_handle(stream))
+        self._check(st)
+        return its, change
+
     def set_receivers(self, elements, xi):
         el = np.ascontiguousarray(elements, dtype=np.int64)
         xi = np.ascontiguousarray(xi, dtype=np.float64).reshape(-1, 3)

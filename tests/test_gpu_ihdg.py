@@ -1,0 +1,170 @@
+"""iHDG-II on the GPU (transport) against the oracle's IHDGTransport and the
+paper's results, through the C ABI.
+
+* every iterate equals the oracle's iterate (the local inverses, the
+  neighbour coupling and the update): <= 1e-11 relative L2;
+* finite convergence: the iterate is the direct solution after 3E - 2
+  iterations, and the paper's stopping criterion stops at 3E - 1, on meshes
+  up to the paper's largest 3-D case (16^3, Table of iteration counts);
+* one locally implicit Euler step equals the oracle's direct implicit step;
+* refusals (degree, system, call order).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+from harness import rel_l2
+from oracle.ihdg import IHDGTransport
+
+pytestmark = pytest.mark.gpu
+
+BETA = (1.0, 0.7, 0.4)
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "ihdg_transport_iterations.txt")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__ as g
+    g.build()
+
+
+def _manufactured(x, beta=BETA):
+    X = np.pi * np.asarray(x)
+    s, c = np.sin(X), np.cos(X)
+    ue = np.prod(s, axis=-1)
+    grad = np.pi * np.stack([c[..., 0] * s[..., 1] * s[..., 2], s[..., 0] * c[..., 1] * s[..., 2],
+                             s[..., 0] * s[..., 1] * c[..., 2]], axis=-1)
+    return ue[None], (grad @ np.asarray(beta))[None]
+
+
+def _case(E, N, a=0.0, periodic=False, beta=BETA, oracle_side=True):
+    from paper_1711_01175_gb300 import Solver, reference_nodes
+    mesh = wl.structured_hex_mesh(E, (periodic,) * 3)
+    x_lib = wl.warped_node_coords(mesh, reference_nodes(N)[0], a)
+    s = Solver(N, system="transport", beta=beta)
+    s.upload_mesh(x_lib, mesh.etoe, mesh.etof, mesh.orient, mesh.bc)
+    op = None
+    if oracle_side:
+        x_or = wl.warped_node_coords(mesh, oracle.gll(N)[0], a)
+        op = oracle.FriedrichsDG(N, x_or, mesh.etoe, mesh.etof, mesh.orient, mesh.bc, oracle.transport(beta))
+    return s, op, x_lib, mesh
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("N", [1, 2, 4])
+def test_iterates_match_the_oracle(N):
+    import torch
+    s, op, x, _ = _case(3, N, a=0.05)
+    ih = IHDGTransport(op, 0.0)
+    _, f = _manufactured(x)
+    s.ihdg_setup(0.0)
+    fd = _dev(f)
+    iterates = [np.zeros_like(f)]
+    for _ in range(5):
+        iterates.append(ih.iterate(f, iterates[-1]))
+    for k in (1, 2, 3, 5):
+        u = torch.zeros_like(fd)
+        its, _ = s.ihdg_solve(u, f=fd, tol=0.0, max_iter=k)
+        assert its == k
+        assert rel_l2(u.cpu().numpy(), iterates[k]) < 1e-11, k
+
+
+def test_converged_solution_is_the_direct_solution():
+    import torch
+    s, op, x, _ = _case(3, 3, a=0.05)
+    _, f = _manufactured(x)
+    s.ihdg_setup(0.0)
+    u = torch.zeros((1, op.nel, op.Np), dtype=torch.float64, device="cuda")
+    its, change = s.ihdg_solve(u, f=_dev(f), tol=1e-10)
+    assert its == 3 * 3 - 1 and change < 1e-10
+    ud = IHDGTransport(op, 0.0).direct(f)
+    assert rel_l2(u.cpu().numpy(), ud) < 1e-10
+
+
+def _golden():
+    rows = [l.split() for l in open(GOLDEN) if l.strip() and not l.startswith("#")]
+    return {(int(E), int(p)): int(k) for E, p, k in rows}
+
+
+@pytest.mark.parametrize("E,N", [(4, 4), (8, 3), (16, 2), (16, 4)])
+def test_finite_convergence_and_iteration_counts_up_to_the_papers_largest_mesh(E, N):
+    """Exactness after 3E - 2 iterations (criterion-free: Theorem DDMConvergence,
+    one iteration per diagonal layer of elements), and the count of the paper's
+    stopping criterion with the exact solution (eq. tolerancecriteria), one
+    iteration per call, against its table (3D column) up to 8^3.  On 16^3 the
+    last layers lie in the corner where this manufactured solution is small, so
+    their updates fall below the 1e-10 of the criterion before they are exact and
+    the count (42 for N = 2) depends on the solution, which the paper does not
+    print; there the check is the finite convergence itself."""
+    import torch
+    from paper_1711_01175_gb300 import reference_nodes
+    s, _, x, mesh = _case(E, N, oracle_side=False)
+    ue, f = _manufactured(x)
+    s.ihdg_setup(0.0)
+    fd, ued = _dev(f), _dev(ue)
+    w = reference_nodes(N)[1]
+    wJ = torch.from_numpy(np.einsum("k,j,i->kji", w, w, w).ravel() / (8.0 * E ** 3)).cuda()   # undeformed cells
+
+    def err(u):
+        return float(torch.sqrt(torch.sum(wJ * (u - ued) ** 2)))
+
+    u = torch.zeros((1, mesh.nel, (N + 1) ** 3), dtype=torch.float64, device="cuda")
+    its_exact_rule, prev = None, err(u)
+    for k in range(1, 3 * E + 2):
+        s.ihdg_solve(u, f=fd, tol=0.0, max_iter=1)
+        e_k = err(u)
+        if its_exact_rule is None and abs(e_k - prev) < 1e-10:
+            its_exact_rule = k
+        prev = e_k
+        if k == 3 * E - 2:
+            u_fixed = u.clone()
+    # one iteration from the iterate 3E - 2 changes nothing (finite convergence)
+    _, change = s.ihdg_solve(u_fixed, f=fd, tol=0.0, max_iter=1)
+    assert change < 1e-13 * float(torch.sqrt(torch.sum(wJ * u_fixed ** 2)))
+    paper = _golden()[(E, N)]
+    assert its_exact_rule <= 3 * E - 1
+    if E <= 8:
+        assert 3 * E - 2 <= its_exact_rule and abs(its_exact_rule - paper) <= 1, (its_exact_rule, paper)
+    # the relative-change criterion of the C ABI stops no later than 3E - 1
+    u = torch.zeros_like(u)
+    its, _ = s.ihdg_solve(u, f=fd, tol=1e-10, max_iter=10 * E)
+    assert its <= 3 * E - 1 and (E > 8 or its >= 3 * E - 2)
+    assert err(u) < (0.05 if N >= 3 else 0.2) * err(torch.zeros_like(u))
+
+
+def test_locally_implicit_step_is_the_implicit_euler_step():
+    import torch
+    beta = (0.2, 0.3, -0.1)
+    s, op, x, _ = _case(3, 3, a=0.05, periodic=True, beta=beta)
+    dt = 2.0 * oracle.cfl_dt(1.0, 1.0 / 3, op.c_max(), 3)                 # CFL 2
+    s.ihdg_setup(1.0 / dt)
+    um = wl.transport_periodic(x, beta)
+    u = _dev(um)
+    its, change = s.ihdg_solve(u, u_prev=_dev(um), tol=1e-12, max_iter=200)
+    assert change < 1e-12 and its < 60
+    ud = IHDGTransport(op, 1.0 / dt).direct(um / dt)
+    assert rel_l2(u.cpu().numpy(), ud) < 1e-10
+
+
+def test_refusals():
+    import torch
+    from paper_1711_01175_gb300 import Solver, capi, reference_nodes
+    mesh = wl.structured_hex_mesh(2, (False,) * 3)
+    s5 = Solver(5, system="transport", beta=BETA)
+    s5.upload_mesh(wl.warped_node_coords(mesh, reference_nodes(5)[0], 0.0), mesh.etoe, mesh.etof, mesh.orient, mesh.bc)
+    assert capi.dgw_ihdg_setup(s5._ctx, 0.0, None) == -7
+    s2 = Solver(2, system="transport", beta=BETA)
+    s2.upload_mesh(wl.warped_node_coords(mesh, reference_nodes(2)[0], 0.0), mesh.etoe, mesh.etof, mesh.orient, mesh.bc)
+    u = torch.zeros((1, mesh.nel, 27), dtype=torch.float64, device="cuda")
+    st, _, _ = capi.dgw_ihdg_solve(s2._ctx, None, None, u.data_ptr(), 1e-10, 10, None)
+    assert st == -2
+    assert capi.dgw_ihdg_setup(s2._ctx, -1.0, None) == -1
+    el = Solver(2)
+    assert capi.dgw_ihdg_setup(el._ctx, 0.0, None) == -7
