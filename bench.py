@@ -478,6 +478,88 @@ def run_friedrichs(args, hbm_peak, peak_kind):
     return out
 
 
+def run_ihdg(args):
+    """iHDG-II for transport (the paper's Section 3 and Section 6.1):
+    * steady: beta = (1, 0.7, 0.4) on the undeformed E^3 mesh (E = 16, the
+      largest 3-D case of the paper's iteration table), N = 4, manufactured
+      u^e = prod sin(pi x_i); set-up time, iterations to the 1e-10 criterion,
+      solve time, time per iteration (two launches and the stopping test's host
+      round trip) and the iteration kernel's FP64 rate (2 Np^2 flops per element
+      for the local inverse);
+    * locally implicit: implicit Euler steps of the periodic transport test
+      (beta = (0.2, 0.2, 0.2)) at CFL 1, 2 and 5: iterations per step."""
+    import torch
+    from paper_1711_01175_gb300 import Solver, reference_nodes
+    N, E = 4, args.ihdg_E
+    r, _ = reference_nodes(N)
+    mesh = wl.structured_hex_mesh(E, (False, False, False), order="morton")
+    x = wl.warped_node_coords(mesh, r, 0.0)
+    beta = np.array([1.0, 0.7, 0.4])
+    X = np.pi * x
+    sn, cs = np.sin(X), np.cos(X)
+    ue = np.prod(sn, axis=-1)[None]
+    grad = np.pi * np.stack([cs[..., 0] * sn[..., 1] * sn[..., 2], sn[..., 0] * cs[..., 1] * sn[..., 2],
+                             sn[..., 0] * sn[..., 1] * cs[..., 2]], axis=-1)
+    f = torch.from_numpy((grad @ beta)[None]).cuda()
+    s = Solver(N, system="transport", beta=beta)
+    s.upload_mesh(x, mesh.etoe, mesh.etof, mesh.orient, mesh.bc)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.ihdg_setup(0.0)
+    setup_s = time.perf_counter() - t0
+    u = torch.zeros_like(f)
+    s.ihdg_solve(u, f=f, tol=0.0, max_iter=2)            # warm-up
+    u.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    its, change = s.ihdg_solve(u, f=f, tol=1e-10, max_iter=20 * E)
+    solve_s = time.perf_counter() - t0
+    err = float(np.linalg.norm(u.cpu().numpy() - ue) / np.linalg.norm(ue))
+    Np = (N + 1) ** 3
+    flops = 2.0 * Np * Np * mesh.nel * its
+    table = {}
+    with open(os.path.join(ROOT, "tests", "golden", "ihdg_transport_iterations.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                e_, p_, k_ = (int(v) for v in line.split())
+                table[(e_, p_)] = k_
+    steady = {"mesh": f"{E}^3", "N": N, "iterations": its, "element_layers_plus_one": 3 * E - 1,
+              "paper_table_iterations": table.get((E, N)),
+              "last_change": change, "setup_s": setup_s, "solve_ms": solve_s * 1e3,
+              "ms_per_iteration": solve_s * 1e3 / its, "rel_l2_error_vs_exact": err,
+              "matvec_fp64_tflops": flops / solve_s / 1e12,
+              "matvec_frac_of_fp64_peak": flops / solve_s / 1e12 / FP64_PEAK_TFLOPS,
+              "inverse_bytes": Np * Np * 8 * mesh.nel}
+    s.close()
+    del u, f
+    # locally implicit Euler steps
+    Ei = args.ihdg_implicit_E
+    mesh = wl.structured_hex_mesh(Ei, order="morton")
+    x = wl.warped_node_coords(mesh, r, 0.05)
+    b2 = (0.2, 0.2, 0.2)
+    implicit = []
+    for cfl in (1.0, 2.0, 5.0):
+        s = Solver(N, system="transport", beta=b2, cfl=cfl)
+        s.upload_mesh(x, mesh.etoe, mesh.etof, mesh.orient, mesh.bc)
+        dt = s.dt_cfl()
+        s.ihdg_setup(1.0 / dt)
+        um = torch.from_numpy(wl.transport_periodic(x, b2)).cuda()
+        u = um.clone()
+        counts = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.ihdg_steps):
+            k, _ = s.ihdg_solve(u, u_prev=um, tol=1e-10, max_iter=500)
+            counts.append(k)
+            um.copy_(u)
+        wall = time.perf_counter() - t0
+        implicit.append({"cfl": cfl, "dt": dt, "steps": args.ihdg_steps, "iterations_per_step": counts,
+                         "ms_per_step": wall * 1e3 / args.ihdg_steps})
+        s.close()
+    return {"steady": steady, "locally_implicit": {"mesh": f"{Ei}^3", "N": N, "beta": list(b2), "runs": implicit},
+            "precision": "fp64"}
+
+
 def build_workload_oracle(name, E=None):
     import oracle
     cfg = workload_config(name, E)
@@ -502,6 +584,10 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-friedrichs", action="store_true", help="skip the transport / shallow-water section")
+    ap.add_argument("--no-ihdg", action="store_true", help="skip the iHDG-II section")
+    ap.add_argument("--ihdg-E", type=int, default=16)
+    ap.add_argument("--ihdg-implicit-E", type=int, default=16)
+    ap.add_argument("--ihdg-steps", type=int, default=5)
     ap.add_argument("--fr-E", type=int, default=64, help="transport mesh edge (shallow water: 8x this, one layer)")
     ap.add_argument("--fr-steps", type=int, default=20)
     ap.add_argument("--adj-E", type=int, default=16, help="adjoint mesh edge (the full recipe: 32)")
@@ -614,6 +700,8 @@ def main():
     if world == 1 and not args.no_friedrichs:
         hbm_peak_f, peak_kind_f = peaks()
         line["friedrichs"] = run_friedrichs(args, hbm_peak_f, peak_kind_f)
+    if world == 1 and not args.no_ihdg:
+        line["ihdg"] = run_ihdg(args)
     if len(results) > 1:
         m = results["mixed"]
         line["variants"] = {"mixed": {"value": m["value"], "dtype": "f32/f64", "steps": m["steps"],
