@@ -174,6 +174,26 @@ def setup_solver(precision, cfg, data):
     return s
 
 
+def whole_job_rate(local_ms, local_units, device=None):
+    """Whole-job throughput of a replicated run: the units every rank processed
+    divided by the slowest rank's time (MAX all-reduce of the time, SUM of the
+    units; a single process returns its own figures).  Returns (units/s, max ms)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(local_units)], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    max_ms = float(t.item())
+    return float(u.item()) / (max_ms * 1e-3), max_ms
+
+
+def energy_reduction_launches(stage_ctas):
+    """Kernels of the fused energy's final reduction (one block up to 2048 partials, two levels above)."""
+    return 1 if stage_ctas <= 8 * 256 else 2
+
+
 def run_variant(precision, cfg, data, steps, warmup, device, stream, clocks=None):
     """Device-resident timing: K steps of 5 stage launches + 1 energy launch pair."""
     import torch
@@ -222,6 +242,9 @@ def run_variant(precision, cfg, data, steps, warmup, device, stream, clocks=None
     for k in range(steps):
         one_step(ev[k])
     t1.record(stream)
+    torch.cuda.synchronize(device)
+    if torch.distributed.is_initialized():
+        torch.distributed.barrier()
     torch.cuda.synchronize(device)
     clk = clocks.stop() if clocks else None
     total_ms = t0.elapsed_time(t1)
@@ -635,17 +658,15 @@ def main():
         clk = Clocks(local)
         r = run_variant(prec, cfg, data, k, args.warmup, device, stream, clk)
         r["steps"] = k
-        total = torch.tensor([r["total_ms"]], device=device)
-        if world > 1:
-            torch.distributed.all_reduce(total, op=torch.distributed.ReduceOp.MAX)
-        r["max_ms"] = float(total.item())
-        r["value"] = world * r["dof"] * 5 * k / (r["max_ms"] * 1e-3)
+        r["value"], r["max_ms"] = whole_job_rate(r["total_ms"], r["dof"] * 5 * k, device)
         if not args.no_e2e:
             e = run_e2e(prec, cfg, data, max(2, k // 4), args.warmup, device, stream)
             r["e2e"] = {"value": r["dof"] * 5 * max(2, k // 4) / (e["ms"] * 1e-3) * world, "unit": UNIT,
                         "h2d_bytes_per_step": e["h2d_bytes_per_step"],
                         "d2h_bytes_per_step": e["d2h_bytes_per_step"]}
-        launches_per_step = 5 + 1          # five stage launches + the energy's final reduction
+        # five stage launches + the final reduction of the fused energy's per-CTA partials
+        epb = {1: 16, 2: 9, 3: 4}.get(cfg.N, 1)
+        launches_per_step = 5 + energy_reduction_launches((r["nel"] + epb - 1) // epb)
         r["gpu_launches"] = launches_per_step * k
         N = cfg.N
         if prec == "fp64":
