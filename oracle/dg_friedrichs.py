@@ -94,6 +94,7 @@ class FriedrichsDG(ElasticDG):
         super().__init__(N, x, etoe, etof, orient, bc, one, one, one, tau)
         self.system = system
         self.m = system.m
+        self.self_only = False      # True: interior neighbour states taken as zero (L_K^self)
 
     def set_point_force(self, *args, **kwargs):
         raise NotImplementedError("point forces are defined for the elastic system only")
@@ -109,7 +110,8 @@ class FriedrichsDG(ElasticDG):
             raise ValueError(f"face {f}: element without neighbour and without boundary tag")
         flat = u.reshape(self.m, -1)
         up = np.zeros_like(um)
-        up[:, interior] = flat[:, nbr[interior]]
+        if not self.self_only:
+            up[:, interior] = flat[:, nbr[interior]]
         for t in (1, 2):
             sel = tag == t
             if np.any(sel):

@@ -4,13 +4,16 @@ Algorithm "The iHDG-II approach") on the upwind DG/HDG transport operator.
 TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and
 ``bench.py`` (its CPU-baseline / reference leg) may import or run this module.
 
-The problem is  sigma u - L(u) = b  with L the semi-discrete transport
-operator of ``FriedrichsDG`` (upwind flux, trace eliminated) and b given:
+The problem is  sigma u - L(u) = b  with L the semi-discrete operator of
+``FriedrichsDG`` (upwind flux, trace eliminated) and b given; for transport:
 * sigma = 0, b = f: the steady transport equation (Section 3.1,
   eq. transport) with forcing f;
 * sigma = 1/dt, b = u^m / dt + f: one implicit Euler step of the
   time-dependent transport equation (Section 3.3, eq. implicitHDG), of which
-  iHDG-II is the locally implicit solver (Section 3.3).
+  iHDG-II is the locally implicit solver (Section 3.3);
+and for the shallow-water system sigma = 2/dt, b = sigma u^m + L(u^m): one
+Crank-Nicolson step, the time scheme of the paper's shallow-water test
+(Section 6.3).
 
 iHDG-II, iteration k -> k+1 (eqs. iHDGlocal and iHDGtrace): every element K
 solves its local problem with its own unknowns at k+1 and its neighbours'
@@ -39,37 +42,47 @@ def element_coloring(etoe):
     return color
 
 
-class IHDGTransport:
+class IHDG:
+    """iHDG-II for a FriedrichsDG operator with m fields; sigma >= 0.
+
+    L_K^self is the operator with the interior neighbour states zero (boundary
+    states keep their dependence on the element's own values), assembled
+    column by column: the unit vector of (field q, node j) in every element at
+    once."""
+
     def __init__(self, op, sigma):
-        """op: a FriedrichsDG of the transport system; sigma >= 0."""
-        if op.m != 1:
-            raise ValueError("iHDG-II oracle: scalar transport only")
         self.op = op
         self.sigma = float(sigma)
-        self.nel, self.Np = op.nel, op.Np
+        self.m, self.nel, self.Np = op.m, op.nel, op.Np
         _, J = op.geometry(np.arange(op.nel))
         self.wJ = op.w_vol[None, :] * J                      # [nel, Np] mass weights
-        # L_K^self for every element: with a colouring, elements of one colour
-        # do not touch, so a unit vector in node j of all of them gives column j
-        # of each one's self block.
-        color = element_coloring(op.etoe)
-        self.Lself = np.zeros((self.nel, self.Np, self.Np))
-        for c in range(int(color.max()) + 1):
-            sel = np.nonzero(color == c)[0]
-            for j in range(self.Np):
-                u = np.zeros((1, self.nel, self.Np))
-                u[0, sel, j] = 1.0
-                self.Lself[sel, :, j] = op.rhs(u)[0, sel]
-        self.local = self.sigma * np.eye(self.Np)[None] - self.Lself      # sigma I - L_K^self
+        n = self.m * self.Np
+        self.Lself = np.zeros((self.nel, n, n))             # rows/columns (field, node), field-major
+        op.self_only = True
+        try:
+            for q in range(self.m):
+                for j in range(self.Np):
+                    u = np.zeros((self.m, self.nel, self.Np))
+                    u[q, :, j] = 1.0
+                    self.Lself[:, :, q * self.Np + j] = np.moveaxis(op.rhs(u), 0, 1).reshape(self.nel, n)
+        finally:
+            op.self_only = False
+        self.local = self.sigma * np.eye(n)[None] - self.Lself      # sigma I - L_K^self
+
+    def _flat(self, u):
+        return np.moveaxis(u, 0, 1).reshape(self.nel, -1)            # [nel, m Np]
+
+    def _unflat(self, v):
+        return np.moveaxis(v.reshape(self.nel, self.m, self.Np), 1, 0)
 
     def neighbour_term(self, u):
-        """L_K^nbr(u) = L(u)_K - L_K^self u_K for every element: [1, nel, Np]."""
-        return self.op.rhs(u) - np.einsum("eij,ej->ei", self.Lself, u[0])[None]
+        """L_K^nbr(u) = L(u)_K - L_K^self u_K for every element: [m, nel, Np]."""
+        return self.op.rhs(u) - self._unflat(np.einsum("eij,ej->ei", self.Lself, self._flat(u)))
 
     def iterate(self, b, u):
         """One iHDG-II iteration from u^k: the local solves of every element."""
-        rhs = b + self.neighbour_term(u)
-        return np.linalg.solve(self.local, rhs[0][..., None])[..., 0][None]
+        rhs = self._flat(b + self.neighbour_term(u))
+        return self._unflat(np.linalg.solve(self.local, rhs[..., None])[..., 0])
 
     def norm(self, d):
         return float(np.sqrt(np.sum(self.wJ[None] * d * d)))
@@ -95,10 +108,19 @@ class IHDGTransport:
 
     def direct(self, b):
         """The fixed point by a direct solve of sigma u - L(u) = b (assembled by columns)."""
-        n = self.nel * self.Np
+        n = self.m * self.nel * self.Np
         A = np.zeros((n, n))
         for j in range(n):
             e = np.zeros(n)
             e[j] = 1.0
-            A[:, j] = self.sigma * e - self.op.rhs(e.reshape(1, self.nel, self.Np)).ravel()
+            A[:, j] = self.sigma * e - self.op.rhs(e.reshape(self.m, self.nel, self.Np)).ravel()
         return np.linalg.solve(A, b.ravel()).reshape(b.shape)
+
+
+class IHDGTransport(IHDG):
+    """iHDG-II for the scalar transport operator."""
+
+    def __init__(self, op, sigma):
+        if op.m != 1:
+            raise ValueError("IHDGTransport: scalar transport only")
+        super().__init__(op, sigma)

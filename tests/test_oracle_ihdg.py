@@ -108,3 +108,56 @@ def test_locally_implicit_step_equals_the_direct_implicit_step():
     u, its, hist = ih.solve(b, um, tol=1e-12)
     assert its < 40 and hist[-1] < 1e-12
     assert ih.norm(u - ud) < 1e-10 * ih.norm(ud)
+
+
+# ---- the linearized shallow-water system, Crank-Nicolson (Section 6.3) -------
+
+SW_GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "ihdg_shallow_water_iterations.txt")
+
+
+def _sw_golden():
+    rows = [l.split() for l in open(SW_GOLDEN) if l.strip() and not l.startswith("#")]
+    return {(int(n), int(p)): (int(a), int(b)) for n, p, a, b in rows}
+
+
+def _sw_op(E, N):
+    mesh = wl.structured_hex_mesh((E, E, 1), (False, False, True), {0: wl.BC_WALL, 1: wl.BC_WALL,
+                                                                     2: wl.BC_WALL, 3: wl.BC_WALL})
+    r, _ = oracle.gll(N)
+    x = wl.warped_node_coords(mesh, r, 0.0)
+    return oracle.FriedrichsDG(N, x, mesh.etoe, mesh.etof, mesh.orient, mesh.bc, oracle.shallow_water()), x
+
+
+def _cn_step(op, x, dt):
+    """sigma = 2/dt, b = sigma u^m + L(u^m) from the standing wave at t = 0."""
+    from oracle.ihdg import IHDG
+    ih = IHDG(op, 2.0 / dt)
+    um = wl.shallow_water_standing_wave(x)
+    return ih, um, ih.sigma * um + op.rhs(um)
+
+
+def test_shallow_water_cn_step_converges_to_the_direct_step():
+    op, x = _sw_op(3, 2)
+    ih, um, b = _cn_step(op, x, 0.1)
+    u, its, hist = ih.solve(b, um, tol=1e-12)
+    assert hist[-1] < 1e-12
+    ud = ih.direct(b)
+    assert ih.norm(u - ud) < 1e-10 * ih.norm(ud)
+    # the Crank-Nicolson step approximates the standing wave at t = dt (coarse mesh: a sanity bound)
+    assert ih.norm(ud - wl.shallow_water_standing_wave(x, 0.1)) < 0.05 * ih.norm(ud)
+
+
+@pytest.mark.parametrize("E,N", [(4, 1), (8, 1), (16, 1), (4, 2), (8, 2)])
+def test_shallow_water_iteration_counts_of_the_paper(E, N):
+    """The paper's iHDG-II counts (golden table), with eq. tolerancecriteriarelerror
+    on the first Crank-Nicolson step: within 3 for both time steps; more
+    iterations for the larger step (the count grows with dt)."""
+    op, x = _sw_op(E, N)
+    paper = _sw_golden()[(E * E, N)]
+    counts = []
+    for dt in (0.1, 0.01):
+        ih, um, b = _cn_step(op, x, dt)
+        _, its, _ = ih.solve(b, um, tol=1e-10)
+        counts.append(its)
+    assert abs(counts[0] - paper[0]) <= 3 and abs(counts[1] - paper[1]) <= 3, (counts, paper)
+    assert counts[0] > counts[1]
