@@ -276,26 +276,31 @@ const char* dgw_batch_last_error(const dgw_batch* b);
 dgw_status dgw_energy_static(int N, int64_t nel, const double* x, const double* u, const double* rho,
                              const double* lam, const double* mu, double* energy_out, void* stream);
 
-/* ---- iHDG-II: the paper's locally implicit iteration (transport) -------
+/* ---- iHDG-II: the paper's locally implicit iteration ---------------------
  * The paper's iHDG-II algorithm (Section 3, Algorithm "The iHDG-II
  * approach"; eqs. iHDGlocal and iHDGtrace) for sigma u - L(u) = b with L the
- * upwind transport operator of a DGW_SYSTEM_TRANSPORT context: every element
+ * upwind operator of a transport or shallow-water context: every element
  * solves its local problem with its own unknowns at iteration k+1 and its
  * neighbours' at k in the weighted trace,
- *     (sigma I - L_K^self) u_K^{k+1} = b_K + L_K^nbr(u^k).
- * sigma = 0 is the steady transport equation (Section 3.1, forcing f);
- * sigma = 1/dt with b = u^m/dt + f is one implicit Euler step solved
- * element by element (Section 3.3, the locally implicit method).  N <= 4. */
+ *     (sigma I - L_K^self) u_K^{k+1} = b_K + L_K^nbr(u^k),
+ * L_K^self being L with the interior neighbour states zero.  Transport:
+ * sigma = 0 is the steady equation (Section 3.1, forcing f); sigma = 1/dt
+ * with b = u^m/dt + f is one implicit Euler step solved element by element
+ * (Section 3.3, the locally implicit method).  Shallow water: sigma = 2/dt
+ * with b = sigma u^m + L(u^m) (f = dgw_rhs of u^m) is one Crank-Nicolson
+ * step (Section 6.3).  Degrees: transport N <= 4, shallow water N <= 2 (the
+ * local block of m Np rows is inverted in shared memory). */
 
 /* Build and invert sigma I - L_K^self for every element (device memory:
- * nel * Np^2 doubles, about 1 MB per 8 elements at N = 4).  sigma >= 0.
- * DGW_ERR_UNSUPPORTED unless the context is transport with N <= 4;
+ * nel * (m Np)^2 doubles, about 1 MB per 8 elements for transport at N = 4).
+ * sigma >= 0.  DGW_ERR_UNSUPPORTED for elastic contexts and beyond the degrees
+ * above;
  * DGW_ERR_STATE before the mesh; DGW_ERR_ARG if a local matrix is
  * singular.  Synchronises `stream`. */
 dgw_status dgw_ihdg_setup(dgw_ctx* ctx, double sigma, void* stream);
 
-/* Iterate from the initial guess in u (device [nel][Np], overwritten with the
- * result) with b = sigma * u_prev + f (device [nel][Np] each; either may be
+/* Iterate from the initial guess in u (device [m][nel][Np], overwritten with
+ * the result) with b = sigma * u_prev + f (device [m][nel][Np] each; either may be
  * NULL for zero; neither may alias u) until ||u^k - u^{k-1}||_{L2} < tol (the
  * paper's eq. tolerancecriteriarelerror, L2 norm of the mass matrix) or
  * max_iter iterations.  *iterations receives the iterations done and

@@ -1,11 +1,13 @@
-// iHDG-II for the transport system (the paper's Section 3, Algorithm "The
-// iHDG-II approach"): solve sigma u - L(u) = b by element-local solves,
+// iHDG-II (the paper's Section 3, Algorithm "The iHDG-II approach") for the
+// transport and shallow-water systems: solve sigma u - L(u) = b by
+// element-local solves,
 //     (sigma I - L_K^self) u_K^{k+1} = b_K + L_K^nbr(u^k),
 // where the weighted trace of eq. iHDGtrace takes the element's own unknowns
 // at k+1 and its neighbours' at k.  With the upwind flux the neighbour
-// coupling of a face node is c (u^+)^k with
-//     c = -(1/(w_0 J)) 1/2 (beta.m - tau |beta.m|),   m = n sJ outward,
-// non-zero on inflow faces only.
+// coupling of a face node is the m x m matrix
+//     C = -(1/(w_0 J)) 1/2 (A(m) - tau S(m)),   m = n sJ outward,
+// applied to (u^+)^k: for transport the scalar -(1/(w_0 J)) 1/2 (beta.m -
+// tau |beta.m|), non-zero on inflow faces only.
 //
 // Set-up (dgw_ihdg_setup): L_K^self column by column from the transport stage
 // kernel in its self-only mode (neighbour states zero) applied to the unit
@@ -25,21 +27,32 @@
 namespace dgw {
 namespace {
 
-constexpr int kIhdgMaxN = 4;   // the inverse of a degree-4 element (125 x 125) fills 122 KB of shared memory
+// Degrees built: the local block has m Np rows and must fit shared memory
+// (transport N = 4: 125 x 125, 122 KB; shallow water N = 2: 81 x 81).
+constexpr int kIhdgMaxNTransport = 4;
+constexpr int kIhdgMaxNShallow = 2;
 
-__global__ void unit_column_kernel(double* u, long long total, int Np, int j) {
+// Unit vector of (field q, node j) in every element of an [m][nel][Np] state.
+__global__ void unit_column_kernel(double* u, long long nodes, int Np, int m, int q, int j) {
+  const long long total = nodes * m;
   for (long long g = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; g < total;
        g += static_cast<long long>(gridDim.x) * blockDim.x)
-    u[g] = (g % Np) == j ? 1.0 : 0.0;
+    u[g] = (g / nodes == q && (g % nodes) % Np == j) ? 1.0 : 0.0;
 }
 
-// A[e][i][j] = sigma delta_ij - col[e][i]  (row-major blocks)
-__global__ void scatter_column_kernel(const double* col, double* A, long long total, int Np, int j, double sigma) {
+// Column (q, j) of every block: A[e][(p, i)][(q, j)] = sigma delta - col[p][e][i]
+// (row-major blocks of n = m Np, rows and columns field-major).
+__global__ void scatter_column_kernel(const double* col, double* A, long long nodes, int Np, int m, int qj,
+                                      double sigma) {
+  const int n = m * Np;
+  const long long total = nodes * m;
   for (long long g = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; g < total;
        g += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const long long e = g / Np;
-    const int i = static_cast<int>(g - e * Np);
-    A[(e * Np + i) * Np + j] = (i == j ? sigma : 0.0) - col[g];
+    const int p = static_cast<int>(g / nodes);
+    const long long rem = g - static_cast<long long>(p) * nodes;
+    const long long e = rem / Np;
+    const int row = p * Np + static_cast<int>(rem - e * Np);
+    A[(e * n + row) * n + qj] = (row == qj ? sigma : 0.0) - col[g];
   }
 }
 
@@ -123,8 +136,8 @@ __global__ void __launch_bounds__(256) gj_invert_kernel(double* A, int n, long l
   }
 }
 
-// c of every face node of every element (zero on boundary faces and outflow faces).
-template <int N>
+// C of every face node of every element (zero on boundary faces), m x m row-major.
+template <int N, int M>
 __global__ void face_coef_kernel(const double* geo, const int* vmapP, long long nel, double beta0, double beta1,
                                  double beta2, double tau, double w_end_inv, double* cf) {
   constexpr int n = N + 1, Np = n * n * n, nf = n * n;
@@ -134,7 +147,9 @@ __global__ void face_coef_kernel(const double* geo, const int* vmapP, long long 
        g += static_cast<long long>(gridDim.x) * blockDim.x) {
     const long long e = g / (6 * nf);
     const int r = static_cast<int>(g - e * 6 * nf);
-    double c = 0.0;
+    double C[M * M];
+#pragma unroll
+    for (int q = 0; q < M * M; ++q) C[q] = 0.0;
     if (vmapP[g] >= 0) {
       const int f = r / nf, pf = r - (r / nf) * nf, d = f >> 1;
       const bool hi = (f & 1) != 0;
@@ -144,83 +159,119 @@ __global__ void face_coef_kernel(const double* geo, const int* vmapP, long long 
       const int c2 = d == 2 ? cd : fb;
       const size_t gi = static_cast<size_t>(e) * Np + c0 + n * (c1 + n * c2);
       const double sgn = hi ? 1.0 : -1.0;
-      const double bm = sgn * (beta0 * geo[(3 * d + 0) * fstride + gi] + beta1 * geo[(3 * d + 1) * fstride + gi] +
-                               beta2 * geo[(3 * d + 2) * fstride + gi]);
-      c = -0.5 * w_end_inv * geo[9 * fstride + gi] * (bm - tau * fabs(bm));
+      const double m1 = sgn * geo[(3 * d + 0) * fstride + gi];
+      const double m2 = sgn * geo[(3 * d + 1) * fstride + gi];
+      const double m3 = sgn * geo[(3 * d + 2) * fstride + gi];
+      const double s = -0.5 * w_end_inv * geo[9 * fstride + gi];
+      if constexpr (M == 1) {
+        const double bm = beta0 * m1 + beta1 * m2 + beta2 * m3;
+        C[0] = s * (bm - tau * fabs(bm));
+      } else {
+        // A(m) = [[0, m1, m2], [m1, 0, 0], [m2, 0, 0]];
+        // S(m) = [[nu, 0, 0], [0, m1^2/nu, m1 m2/nu], [0, m1 m2/nu, m2^2/nu]], nu = |(m1, m2)|
+        const double nu = sqrt(m1 * m1 + m2 * m2);
+        const double inu = nu > 0.0 ? 1.0 / nu : 0.0;
+        C[0] = -s * tau * nu;
+        C[1] = s * m1;
+        C[2] = s * m2;
+        C[3] = s * m1;
+        C[4] = -s * tau * m1 * m1 * inu;
+        C[5] = -s * tau * m1 * m2 * inu;
+        C[6] = s * m2;
+        C[7] = -s * tau * m1 * m2 * inu;
+        C[8] = -s * tau * m2 * m2 * inu;
+      }
     }
-    cf[g] = c;
+#pragma unroll
+    for (int q = 0; q < M * M; ++q) cf[g * M * M + q] = C[q];
   }
 }
 
-// One iHDG-II iteration: u_next_K = inv_K (sigma u_prev_K + f_K + sum_faces c u_k^+),
-// and part[e] = sum_i w J (u_next - u_k)^2 over the element.
-template <int N>
-__global__ void __launch_bounds__(((N + 1) * (N + 1) * (N + 1) + 31) / 32 * 32)
+// One iHDG-II iteration: u_next_K = inv_K (sigma u_prev_K + f_K + sum_faces C u_k^+),
+// and part[e] = sum_(p,i) w J (u_next - u_k)^2 over the element.
+template <int N, int M>
+__global__ void __launch_bounds__((M * (N + 1) * (N + 1) * (N + 1) + 31) / 32 * 32)
     ihdg_iter_kernel(const double* __restrict__ invT, const double* __restrict__ cf, const int* __restrict__ vmapP,
                      const double* __restrict__ wJ, const double* u_prev, const double* f, double sigma,
                      const double* __restrict__ uk, double* __restrict__ unext, long long nel, double* part) {
-  constexpr int n = N + 1, Np = n * n * n, nf = n * n, NT = (Np + 31) / 32 * 32;
-  __shared__ double rhs_s[Np];
-  __shared__ double x_s[6 * nf];
+  constexpr int n = N + 1, Np = n * n * n, nf = n * n, NB = M * Np, NT = (NB + 31) / 32 * 32;
+  __shared__ double rhs_s[NB];
+  __shared__ double x_s[6 * nf * M];
   __shared__ double red[32];
   const long long e = blockIdx.x;
   const int t = threadIdx.x;
+  const size_t fstride = static_cast<size_t>(nel) * Np;
   for (int r = t; r < 6 * nf; r += NT) {
     const size_t gr = static_cast<size_t>(e) * 6 * nf + r;
     const int g = vmapP[gr];
-    x_s[r] = g >= 0 ? cf[gr] * uk[g] : 0.0;
+#pragma unroll
+    for (int p = 0; p < M; ++p) {
+      double x = 0.0;
+      if (g >= 0) {
+#pragma unroll
+        for (int q = 0; q < M; ++q) x += cf[gr * M * M + p * M + q] * uk[q * fstride + g];
+      }
+      x_s[r * M + p] = x;
+    }
   }
   __syncthreads();
-  double rhs = 0.0;
-  const size_t gi = static_cast<size_t>(e) * Np + t;
-  if (t < Np) {
-    rhs = (u_prev ? sigma * u_prev[gi] : 0.0) + (f ? f[gi] : 0.0);
-    const int ix = t % n, iy = (t / n) % n, iz = t / nf;
-    if (ix == 0) rhs += x_s[0 * nf + iy + n * iz];
-    if (ix == N) rhs += x_s[1 * nf + iy + n * iz];
-    if (iy == 0) rhs += x_s[2 * nf + ix + n * iz];
-    if (iy == N) rhs += x_s[3 * nf + ix + n * iz];
-    if (iz == 0) rhs += x_s[4 * nf + ix + n * iy];
-    if (iz == N) rhs += x_s[5 * nf + ix + n * iy];
+  const int p = t / Np, i = t - (t / Np) * Np;
+  const size_t gi = p * fstride + static_cast<size_t>(e) * Np + i;
+  if (t < NB) {
+    double rhs = (u_prev ? sigma * u_prev[gi] : 0.0) + (f ? f[gi] : 0.0);
+    const int ix = i % n, iy = (i / n) % n, iz = i / nf;
+    if (ix == 0) rhs += x_s[(0 * nf + iy + n * iz) * M + p];
+    if (ix == N) rhs += x_s[(1 * nf + iy + n * iz) * M + p];
+    if (iy == 0) rhs += x_s[(2 * nf + ix + n * iz) * M + p];
+    if (iy == N) rhs += x_s[(3 * nf + ix + n * iz) * M + p];
+    if (iz == 0) rhs += x_s[(4 * nf + ix + n * iy) * M + p];
+    if (iz == N) rhs += x_s[(5 * nf + ix + n * iy) * M + p];
     rhs_s[t] = rhs;
   }
   __syncthreads();
   double v = 0.0;
-  if (t < Np) {
-    const double* M = invT + static_cast<size_t>(e) * Np * Np + t;
+  if (t < NB) {
+    const double* Mt = invT + static_cast<size_t>(e) * NB * NB + t;
     double acc = 0.0;
-#pragma unroll 5
-    for (int j = 0; j < Np; ++j) acc = fma(M[static_cast<size_t>(j) * Np], rhs_s[j], acc);
+#pragma unroll 3
+    for (int j = 0; j < NB; ++j) acc = fma(Mt[static_cast<size_t>(j) * NB], rhs_s[j], acc);
     unext[gi] = acc;
     const double d = acc - uk[gi];
-    v = wJ[gi] * d * d;
+    v = wJ[static_cast<size_t>(e) * Np + i] * d * d;
   }
   for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
   if ((t & 31) == 0) red[t >> 5] = v;
   __syncthreads();
   if (t == 0) {
-    double s = 0.0;
-    for (int w = 0; w < NT / 32; ++w) s += red[w];
-    part[e] = s;
+    double sum = 0.0;
+    for (int w = 0; w < NT / 32; ++w) sum += red[w];
+    part[e] = sum;
   }
 }
 
-template <int N>
+template <int N, int M>
 cudaError_t launch_iter(const dgw_ctx* c, const double* u_prev, const double* f, const double* uk, double* unext,
                         cudaStream_t s) {
-  constexpr int Np = (N + 1) * (N + 1) * (N + 1), NT = (Np + 31) / 32 * 32;
-  ihdg_iter_kernel<N><<<(unsigned)c->nel, NT, 0, s>>>(c->ihdg_inv, c->ihdg_cf, c->vmapP, c->wJ, u_prev, f,
-                                                       c->ihdg_sigma, uk, unext, c->nel, c->ihdg_part);
+  constexpr int NB = M * (N + 1) * (N + 1) * (N + 1), NT = (NB + 31) / 32 * 32;
+  ihdg_iter_kernel<N, M><<<(unsigned)c->nel, NT, 0, s>>>(c->ihdg_inv, c->ihdg_cf, c->vmapP, c->wJ, u_prev, f,
+                                                          c->ihdg_sigma, uk, unext, c->nel, c->ihdg_part);
   return cudaGetLastError();
 }
 
 cudaError_t launch_iter_any(const dgw_ctx* c, const double* u_prev, const double* f, const double* uk, double* unext,
                             cudaStream_t s) {
+  if (c->cfg.system == DGW_SYSTEM_SHALLOW_WATER) {
+    switch (c->cfg.N) {
+      case 1: return launch_iter<1, 3>(c, u_prev, f, uk, unext, s);
+      case 2: return launch_iter<2, 3>(c, u_prev, f, uk, unext, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (c->cfg.N) {
-    case 1: return launch_iter<1>(c, u_prev, f, uk, unext, s);
-    case 2: return launch_iter<2>(c, u_prev, f, uk, unext, s);
-    case 3: return launch_iter<3>(c, u_prev, f, uk, unext, s);
-    case 4: return launch_iter<4>(c, u_prev, f, uk, unext, s);
+    case 1: return launch_iter<1, 1>(c, u_prev, f, uk, unext, s);
+    case 2: return launch_iter<2, 1>(c, u_prev, f, uk, unext, s);
+    case 3: return launch_iter<3, 1>(c, u_prev, f, uk, unext, s);
+    case 4: return launch_iter<4, 1>(c, u_prev, f, uk, unext, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -231,12 +282,13 @@ cudaError_t launch_face_coef(const dgw_ctx* c, cudaStream_t s) {
   const double wi = 1.0 / c->ref.w[0];
   const double* b = c->cfg.beta;
   const int blocks = 4 * c->sm_count;
-  switch (c->cfg.N) {
-#define DGW_FC(NN)                                                                                          \
-  case NN:                                                                                                  \
-    face_coef_kernel<NN><<<blocks, 256, 0, s>>>(geo, c->vmapP, c->nel, b[0], b[1], b[2], tau, wi, c->ihdg_cf); \
+  const bool sw = c->cfg.system == DGW_SYSTEM_SHALLOW_WATER;
+  switch (c->cfg.N * 2 + (sw ? 1 : 0)) {
+#define DGW_FC(NN, MM, KEY)                                                                                     \
+  case KEY:                                                                                                     \
+    face_coef_kernel<NN, MM><<<blocks, 256, 0, s>>>(geo, c->vmapP, c->nel, b[0], b[1], b[2], tau, wi, c->ihdg_cf); \
     break;
-    DGW_FC(1) DGW_FC(2) DGW_FC(3) DGW_FC(4)
+    DGW_FC(1, 1, 2) DGW_FC(2, 1, 4) DGW_FC(3, 1, 6) DGW_FC(4, 1, 8) DGW_FC(1, 3, 3) DGW_FC(2, 3, 5)
 #undef DGW_FC
     default:
       return cudaErrorInvalidValue;
@@ -286,22 +338,27 @@ extern "C" {
 
 dgw_status dgw_ihdg_setup(dgw_ctx* c, double sigma, void* stream) {
   if (!c) return dgw::ifail(nullptr, DGW_ERR_ARG, "null context");
-  if (c->cfg.system != DGW_SYSTEM_TRANSPORT) return dgw::ifail(c, DGW_ERR_UNSUPPORTED, "iHDG-II is built for transport");
-  if (c->cfg.N > dgw::kIhdgMaxN) return dgw::ifail(c, DGW_ERR_UNSUPPORTED, "iHDG-II is built for N <= 4");
+  if (c->cfg.system == DGW_SYSTEM_ELASTIC)
+    return dgw::ifail(c, DGW_ERR_UNSUPPORTED, "iHDG-II is built for transport and shallow water");
+  if (c->cfg.system == DGW_SYSTEM_TRANSPORT && c->cfg.N > dgw::kIhdgMaxNTransport)
+    return dgw::ifail(c, DGW_ERR_UNSUPPORTED, "iHDG-II for transport is built for N <= 4");
+  if (c->cfg.system == DGW_SYSTEM_SHALLOW_WATER && c->cfg.N > dgw::kIhdgMaxNShallow)
+    return dgw::ifail(c, DGW_ERR_UNSUPPORTED, "iHDG-II for shallow water is built for N <= 2");
   if (!c->has_mesh) return dgw::ifail(c, DGW_ERR_STATE, "iHDG-II set-up before the mesh");
   if (!(sigma >= 0.0) || !std::isfinite(sigma)) return dgw::ifail(c, DGW_ERR_ARG, "sigma must be finite and >= 0");
   if (cudaSetDevice(c->device) != cudaSuccess) return dgw::ifail(c, DGW_ERR_CUDA, "cudaSetDevice");
   cudaStream_t s = (cudaStream_t)stream;
-  const int N = c->cfg.N, n = N + 1, Np = n * n * n, nf = n * n;
+  const int N = c->cfg.N, n = N + 1, Np = n * n * n, nf = n * n, m = c->m, nb = m * Np;
   const long long nel = c->nel;
   const size_t nodes = static_cast<size_t>(nel) * Np;
   dgw::ihdg_free(c);
-  if (cudaMalloc(&c->ihdg_inv, nodes * Np * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&c->ihdg_cf, static_cast<size_t>(nel) * 6 * nf * sizeof(double)) != cudaSuccess ||
+  const size_t inv_bytes = static_cast<size_t>(nel) * nb * nb * sizeof(double);
+  if (cudaMalloc(&c->ihdg_inv, inv_bytes) != cudaSuccess ||
+      cudaMalloc(&c->ihdg_cf, static_cast<size_t>(nel) * 6 * nf * m * m * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&c->ihdg_part, (static_cast<size_t>(nel) + 1 + dgw::kEnergyBlocks) * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&c->ihdg_u2, nodes * sizeof(double)) != cudaSuccess) {
+      cudaMalloc(&c->ihdg_u2, nodes * m * sizeof(double)) != cudaSuccess) {
     dgw::ihdg_free(c);
-    return dgw::ifail(c, DGW_ERR_OOM, "iHDG-II buffers (" + std::to_string(nodes * Np * 8 / (1 << 20)) + " MB of inverses)");
+    return dgw::ifail(c, DGW_ERR_OOM, "iHDG-II buffers (" + std::to_string(inv_bytes >> 20) + " MB of inverses)");
   }
   int* singular = nullptr;
   ICUDA(cudaMalloc(&singular, sizeof(int)), "alloc flag");
@@ -321,12 +378,13 @@ dgw_status dgw_ihdg_setup(dgw_ctx* c, double sigma, void* stream) {
   for (int i = 0; i < n * n; ++i) p.D[i] = c->ref.D[i];
   const int blocks = 4 * c->sm_count;
   cudaError_t e = cudaSuccess;
-  for (int j = 0; j < Np && e == cudaSuccess; ++j) {
-    dgw::unit_column_kernel<<<blocks, 256, 0, s>>>(c->ihdg_u2, static_cast<long long>(nodes), Np, j);
+  for (int qj = 0; qj < nb && e == cudaSuccess; ++qj) {
+    dgw::unit_column_kernel<<<blocks, 256, 0, s>>>(c->ihdg_u2, static_cast<long long>(nodes), Np, m, qj / Np, qj % Np);
     e = cudaGetLastError();
-    if (e == cudaSuccess) e = dgw::launch_friedrichs(DGW_SYSTEM_TRANSPORT, N, false, p, s);
+    if (e == cudaSuccess) e = dgw::launch_friedrichs(c->cfg.system, N, false, p, s);
     if (e == cudaSuccess) {
-      dgw::scatter_column_kernel<<<blocks, 256, 0, s>>>(c->u2, c->ihdg_inv, static_cast<long long>(nodes), Np, j, sigma);
+      dgw::scatter_column_kernel<<<blocks, 256, 0, s>>>(c->u2, c->ihdg_inv, static_cast<long long>(nodes), Np, m, qj,
+                                                         sigma);
       e = cudaGetLastError();
     }
   }
@@ -334,10 +392,10 @@ dgw_status dgw_ihdg_setup(dgw_ctx* c, double sigma, void* stream) {
     cudaFree(singular);
     return dgw::ifail(c, DGW_ERR_CUDA, std::string("local matrices: ") + cudaGetErrorString(e));
   }
-  const size_t smem = static_cast<size_t>(Np) * Np * 8 + Np * 8 + Np * 4;
+  const size_t smem = static_cast<size_t>(nb) * nb * 8 + nb * 8 + nb * 4;
   e = cudaFuncSetAttribute(dgw::gj_invert_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess) {
-    dgw::gj_invert_kernel<<<(unsigned)nel, 256, smem, s>>>(c->ihdg_inv, Np, nel, singular);
+    dgw::gj_invert_kernel<<<(unsigned)nel, 256, smem, s>>>(c->ihdg_inv, nb, nel, singular);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = dgw::launch_face_coef(c, s);
@@ -365,7 +423,8 @@ dgw_status dgw_ihdg_solve(dgw_ctx* c, const double* u_prev, const double* f, dou
   if (u_prev == u || f == u) return dgw::ifail(c, DGW_ERR_ARG, "u must not alias u_prev or f");
   if (cudaSetDevice(c->device) != cudaSuccess) return dgw::ifail(c, DGW_ERR_CUDA, "cudaSetDevice");
   cudaStream_t s = (cudaStream_t)stream;
-  const size_t bytes = static_cast<size_t>(c->nel) * (c->cfg.N + 1) * (c->cfg.N + 1) * (c->cfg.N + 1) * sizeof(double);
+  const size_t bytes =
+      static_cast<size_t>(c->nel) * (c->cfg.N + 1) * (c->cfg.N + 1) * (c->cfg.N + 1) * c->m * sizeof(double);
   double* cur = u;
   double* nxt = c->ihdg_u2;
   double* result = c->ihdg_part + c->nel;

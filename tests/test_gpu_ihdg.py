@@ -168,3 +168,82 @@ def test_refusals():
     assert capi.dgw_ihdg_setup(s2._ctx, -1.0, None) == -1
     el = Solver(2)
     assert capi.dgw_ihdg_setup(el._ctx, 0.0, None) == -7
+
+
+# ---- shallow water, Crank-Nicolson (Section 6.3) ------------------------------
+
+SW_GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "ihdg_shallow_water_iterations.txt")
+
+
+def _sw(E, N, oracle_side=True):
+    from paper_1711_01175_gb300 import Solver, reference_nodes
+    mesh = wl.structured_hex_mesh((E, E, 1), (False, False, True),
+                                  {0: wl.BC_WALL, 1: wl.BC_WALL, 2: wl.BC_WALL, 3: wl.BC_WALL})
+    x_lib = wl.warped_node_coords(mesh, reference_nodes(N)[0], 0.0)
+    s = Solver(N, system="shallow_water")
+    s.upload_mesh(x_lib, mesh.etoe, mesh.etof, mesh.orient, mesh.bc)
+    op = None
+    if oracle_side:
+        x_or = wl.warped_node_coords(mesh, oracle.gll(N)[0], 0.0)
+        op = oracle.FriedrichsDG(N, x_or, mesh.etoe, mesh.etof, mesh.orient, mesh.bc, oracle.shallow_water())
+    return s, op, x_lib, mesh
+
+
+def _gpu_cn_rhs(s, um):
+    """b = (2/dt) u^m + L(u^m): f = L(u^m) from the library's right-hand side."""
+    import torch
+    f = torch.empty_like(um)
+    s.rhs(um, f)
+    return f
+
+
+@pytest.mark.parametrize("N", [1, 2])
+def test_shallow_water_iterates_match_the_oracle(N):
+    import torch
+    from oracle.ihdg import IHDG
+    dt = 0.1
+    s, op, x, mesh = _sw(3, N)
+    ih = IHDG(op, 2.0 / dt)
+    um = wl.shallow_water_standing_wave(x)
+    b = ih.sigma * um + op.rhs(um)
+    iterates = [um]
+    for _ in range(5):
+        iterates.append(ih.iterate(b, iterates[-1]))
+    s.ihdg_setup(2.0 / dt)
+    umd = _dev(um)
+    f = _gpu_cn_rhs(s, umd)
+    for k in (1, 2, 5):
+        u = umd.clone()
+        its, _ = s.ihdg_solve(u, u_prev=umd, f=f, tol=0.0, max_iter=k)
+        assert its == k
+        assert rel_l2(u.cpu().numpy(), iterates[k]) < 1e-11, k
+
+
+def _sw_golden():
+    rows = [l.split() for l in open(SW_GOLDEN) if l.strip() and not l.startswith("#")]
+    return {(int(n), int(p)): (int(a), int(b)) for n, p, a, b in rows}
+
+
+@pytest.mark.parametrize("N", [1, 2])
+def test_shallow_water_counts_on_the_papers_largest_mesh(N):
+    """32 x 32 elements (the table's largest mesh), first Crank-Nicolson step,
+    eq. tolerancecriteriarelerror: within 15 % (at least 3) of the paper's counts
+    for dt = 0.1 and 0.01, and converged (the paper: iHDG-II converges in every
+    case where iHDG-I diverges)."""
+    import torch
+    s, _, x, mesh = _sw(32, N, oracle_side=False)
+    paper = _sw_golden()[(1024, N)]
+    umd = _dev(wl.shallow_water_standing_wave(x))
+    f = _gpu_cn_rhs(s, umd)
+    for dt, want in zip((0.1, 0.01), paper):
+        s.ihdg_setup(2.0 / dt)
+        u = umd.clone()
+        its, change = s.ihdg_solve(u, u_prev=umd, f=f, tol=1e-10, max_iter=1000)
+        assert change < 1e-10
+        assert abs(its - want) <= max(3, 0.15 * want), (dt, its, want)
+
+
+def test_shallow_water_refuses_degrees_above_two():
+    from paper_1711_01175_gb300 import capi
+    s, _, _, _ = _sw(2, 3, oracle_side=False)
+    assert capi.dgw_ihdg_setup(s._ctx, 20.0, None) == -7
