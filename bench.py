@@ -546,6 +546,12 @@ def run_ihdg(args):
             if line.strip() and not line.startswith("#"):
                 e_, p_, k_ = (int(v) for v in line.split())
                 table[(e_, p_)] = k_
+    table_sw = {}
+    with open(os.path.join(ROOT, "tests", "golden", "ihdg_shallow_water_iterations.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                n_, p_, a_, b_ = (int(v) for v in line.split())
+                table_sw[(n_, p_)] = (a_, b_)
     steady = {"mesh": f"{E}^3", "N": N, "iterations": its, "element_layers_plus_one": 3 * E - 1,
               "paper_table_iterations": table.get((E, N)),
               "last_change": change, "setup_s": setup_s, "solve_ms": solve_s * 1e3,
@@ -579,7 +585,29 @@ def run_ihdg(args):
         implicit.append({"cfl": cfl, "dt": dt, "steps": args.ihdg_steps, "iterations_per_step": counts,
                          "ms_per_step": wall * 1e3 / args.ihdg_steps})
         s.close()
+    # shallow water, Crank-Nicolson (the paper's Section 6.3 table: 32 x 32 elements, p = 2)
+    Ns, Es = 2, 32
+    rs, _ = reference_nodes(Ns)
+    mesh = wl.structured_hex_mesh((Es, Es, 1), (False, False, True),
+                                  {0: wl.BC_WALL, 1: wl.BC_WALL, 2: wl.BC_WALL, 3: wl.BC_WALL})
+    x = wl.warped_node_coords(mesh, rs, 0.0)
+    sw = Solver(Ns, system="shallow_water")
+    sw.upload_mesh(x, mesh.etoe, mesh.etof, mesh.orient, mesh.bc)
+    um = torch.from_numpy(wl.shallow_water_standing_wave(x)).cuda()
+    fl = torch.empty_like(um)
+    sw.rhs(um, fl)
+    cn = []
+    for dt in (0.1, 0.01):
+        sw.ihdg_setup(2.0 / dt)
+        u = um.clone()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        k, ch = sw.ihdg_solve(u, u_prev=um, f=fl, tol=1e-10, max_iter=1000)
+        cn.append({"dt": dt, "iterations": k, "paper_table_iterations": table_sw.get((Es * Es, Ns), (None, None))[
+            0 if dt == 0.1 else 1], "solve_ms": (time.perf_counter() - t0) * 1e3})
+    sw.close()
     return {"steady": steady, "locally_implicit": {"mesh": f"{Ei}^3", "N": N, "beta": list(b2), "runs": implicit},
+            "shallow_water_crank_nicolson": {"mesh": f"{Es}x{Es}", "N": Ns, "first_step": cn},
             "precision": "fp64"}
 
 
