@@ -316,6 +316,12 @@ def cpu_oracle_sample(cfg, data, target_s=12.0, nel_sample=512):
                       f"(numpy FP64, 1 thread), {el:.1f} s"}
 
 
+def workload_name(cfg):
+    """The workload as both arms name it in config.workload."""
+    return (cfg.name + f" ({cfg.E}^3 hex, N={cfg.N}, warp {cfg.amplitude}, smooth random medium, free surface top, "
+            "absorbing bottom, x/y periodic)")
+
+
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -348,8 +354,9 @@ def reference_arm(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": cfg.name, "elements": m.nel, "N": N, "precision": "fp64",
-                       "sample_elements": len(elems)},
+            "config": {"workload": workload_name(cfg), "precision": "fp64", "elements": m.nel,
+                       "dof": m.nel * Np * 9, "sample_elements": len(elems),
+                       "parallelism": "rank 0 only (the oracle on host cores)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"one LSRK step (5 stages) per bench step on {len(elems)} of "
                                        f"{m.nel} elements (numpy FP64, 1 thread)"},
@@ -729,8 +736,7 @@ def main():
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if head_prec == "fp64" else "f32/f64",
         "data": "synthetic (seeded mesh, medium and Gaussian pulse of the large workload)",
-        "config": {"workload": cfg.name + f" ({cfg.E}^3 hex, N={cfg.N}, warp {cfg.amplitude}, smooth random "
-                   "medium, free surface top, absorbing bottom, x/y periodic)", "precision": head_prec, "elements": head["nel"],
+        "config": {"workload": workload_name(cfg), "precision": head_prec, "elements": head["nel"],
                    "dof": head["dof"], "step": "one LSRK(5,4) step: 5 fused stage launches, the last one also accumulating the energy of the new state",
                    "l2": f"inputs larger than L2 (state {head['dof'] * 8 / 1e9:.2f} GB per buffer)",
                    "parallelism": f"replicas x{world}"},
