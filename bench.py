@@ -8,8 +8,12 @@ Metric: DOF-stage-updates/s = nel * Np * 9 * 5 * steps / time.
 
 Default run: the FP64 path (every operation in FP64) is the headline line;
 the mixed path (FP32 volume/flux/lift, FP64 Runge-Kutta registers and
-energy) is reported in ``variants.mixed``.  ``--impl reference`` times the
-CPU oracle on a bounded sample of the same workload instead.
+energy) is reported in ``variants.mixed``.  Further sections of the same
+line: ``cpu_baseline`` (the oracle on a bounded sample), ``serving``
+(continuous batching against one-at-a-time solves), ``adjoint`` (gradient
+cost), ``friedrichs`` (transport and shallow-water throughput) and ``ihdg``
+(the iHDG-II iteration).  ``--impl reference`` times the CPU oracle on a
+bounded sample of the same workload instead.
 
 Multi-GPU (torchrun): the path is replicated, one independent solve per rank
 ("replicas only": no data-path collective); value = all ranks' updates / the

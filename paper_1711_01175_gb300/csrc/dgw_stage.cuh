@@ -2,11 +2,15 @@
 // diagonal GLL lift, Q^{-1}, and (optionally) the 2N-storage Runge-Kutta update.
 //
 // One CTA holds EPB elements; thread t owns node t % Np of element t / Np.
-//   1. u of the tile (FP64 in HBM) -> shared memory in Real.
+//   1. u of the tile (FP64 in HBM) -> shared memory in Real, with the metric
+//      terms (node-major packed tiles, 16-byte vector access).
 //   2. Volume term per direction i (eq. LPDE in curvilinear split form):
-//        acc += D_i (A(Ja^i) u)   [conservative part; A(Ja^i)u staged in smem]
+//        acc += D_i (A(Ja^i) u)   [conservative part]
 //        acc += A(Ja^i) (D_i u)   [non-conservative part]
-//      and vol = -1/2 * (1/J) * acc.  A(m)u = -(sigma m, Voigt(sym(m (x) v))).
+//      and vol = -1/2 * (1/J) * acc, with A(m)u = -(sigma m, Voigt(sym(m (x) v))).
+//      FP64 stages A(Ja^i)u of the tile in shared memory per direction; FP32
+//      recomputes A(D_ab Ja^i_b) u_b at each contraction node instead (no
+//      staging, no barrier between directions).
 //   3. Face items (EPB*6*nf of them, spread over all threads): own trace from
 //      smem, neighbour trace from HBM/L2 through the neighbour map (or the
 //      boundary ghost), flux difference 1/2 (A(m) - tau S(m))(u^- - u^+) with
@@ -17,7 +21,8 @@
 //      (1/J)/w_0 and staged in smem.
 //   4. Each node adds the lifted flux of the faces it lies on, applies
 //      Q^{-1} = diag(1/rho, C_V), then writes rhs or performs
-//      res <- a res + dt rhs, u_out <- u_in + b res in FP64.
+//      res <- a res + dt rhs, u_out <- u_in + b res in FP64 (optionally
+//      accumulating the energy of u_out for a fixed-order block sum).
 #pragma once
 
 #include <atomic>
