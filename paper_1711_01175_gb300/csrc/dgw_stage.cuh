@@ -339,20 +339,16 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
         Real Drow[n];
   #pragma unroll
         for (int b = 0; b < n; ++b) Drow[b] = D_s[a * n + b];
-        Real cs[9], ds[9];
+        // D_i (A_+(Ja^i) u) and A_+(Ja^i)(D_i u), both accumulated into acc
+        Real ds[9];
   #pragma unroll
-        for (int q = 0; q < 9; ++q) cs[q] = 0;
+        for (int q = 0; q < 9; ++q) ds[q] = 0;
   #pragma unroll
         for (int b = 0; b < n; ++b) {
           Real F[10];
           V::load9(f_s + (base + b * stride) * PK, F);
   #pragma unroll
-          for (int q = 0; q < 9; ++q) cs[q] += Drow[b] * F[q];
-        }
-  #pragma unroll
-        for (int q = 0; q < 9; ++q) {
-          acc[q] += cs[q];
-          ds[q] = 0;
+          for (int q = 0; q < 9; ++q) acc[q] += Drow[b] * F[q];
         }
   #pragma unroll
         for (int b = 0; b < n; ++b) {
@@ -361,10 +357,7 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
   #pragma unroll
           for (int q = 0; q < 9; ++q) ds[q] += Drow[b] * w[q];
         }
-        Real G[9];
-        apply_Apos(m1, m2, m3, ds, G);
-  #pragma unroll
-        for (int q = 0; q < 9; ++q) acc[q] += G[q];
+        acc_Apos(m1, m2, m3, ds, acc);
       }
       __syncthreads();
     }
