@@ -420,7 +420,12 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
         const size_t fzs = static_cast<size_t>(p.nel) * 6;
         const Real zs = fz[fzi], dz = fz[fzs + fzi], izs = fz[2 * fzs + fzi], diz = fz[3 * fzs + fzi];
         const Real mm = m1 * m1 + m2 * m2 + m3 * m3;
-        const Real isJ = Real(1) / sqrt(mm);
+        Real isJ;
+        if constexpr (std::is_same<Real, double>::value) {
+          isJ = rsqrt(mm);                   // one refinement sequence instead of sqrt and a division
+        } else {
+          isJ = Real(1) / sqrt(mm);
+        }
         const Real sJ = mm * isJ;
         const Real av = dz * (m1 * du[0] + m2 * du[1] + m3 * du[2]) * isJ;
         const Real zsJ = zs * sJ;
