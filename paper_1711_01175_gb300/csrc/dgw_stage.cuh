@@ -367,7 +367,8 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
   {
     const Real* fz = static_cast<const Real*>(p.fz);
     const Real tau = pick<Real>(p.tau, p.tau_f);
-    const Real half_lift = pick<Real>(0.5 * p.w_end_inv, p.hlift_f);
+    // LSRK: the right-hand side is produced already multiplied by dt (Q^{-1} is linear)
+    const Real half_lift = pick<Real>(0.5 * p.w_end_inv, p.hlift_f) * (LSRK ? pick<Real>(p.dt, p.dt_f) : Real(1));
     for (int it = t; it < NFI; it += NT) {
       const int eli = it / (6 * nf);
       const int r = it - eli * (6 * nf);
@@ -495,7 +496,8 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
   if (active) {
     // vol = -1/2 (1/J) (-acc_+) = +1/2 (1/J) acc_+  (acc holds A_+ terms)
     Real r[9];
-    const Real hv = static_cast<Real>(0.5) * g_s[t * PK + gslot_ij<Real>()];
+    const Real hv = static_cast<Real>(0.5) * g_s[t * PK + gslot_ij<Real>()] *
+                    (LSRK ? pick<Real>(p.dt, p.dt_f) : Real(1));
 #pragma unroll
     for (int q = 0; q < 9; ++q) r[q] = hv * sgnA * acc[q];
     const int fb0 = el * 6 * nf;
@@ -554,7 +556,7 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
     if (e == p.src_elem) {
       // point force (already divided by rho and the mass weight at set-up)
 #pragma unroll
-      for (int q = 0; q < 3; ++q) rr[q] += static_cast<Real>(p.src_amp * p.src_w[q * Np + node]);
+      for (int q = 0; q < 3; ++q) rr[q] += static_cast<Real>((LSRK ? p.dt : 1.0) * p.src_amp * p.src_w[q * Np + node]);
     }
 
     if constexpr (!LSRK) {
@@ -575,9 +577,9 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
         const double uq = p.u_in[q * fstride + gidx];     // FP64 state (L2-resident re-read)
         double dtr;
         if constexpr (std::is_same<Real, double>::value) {
-          dtr = p.dt * rr[q];
+          dtr = rr[q];                                // dt already applied
         } else {
-          dtr = widen_int(p.dt_f * rr[q]);
+          dtr = widen_int(rr[q]);
         }
         const double rin = first ? 0.0 : p.res[q * fstride + gidx];
         const double rn = first ? dtr : fma(p.a, rin, dtr);
