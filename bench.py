@@ -445,14 +445,14 @@ def run_adjoint(args):
 def friedrichs_flops_per_node(system, N):
     """FP64 flops of one stage per node as the generic kernel's arithmetic is
     written (n = N + 1; 6 n^2 / n^3 face items per node):
-    transport   volume 3 (A(m)u 6 + two length-n contractions 4n + A(m) du 6 + 2),
-                face item 18, RK update, lift and fused energy 10;
-    shallow water  volume 3 (5 + 12n + 5 + 6), face item 25, update 25."""
+    transport   volume 3 (A(m)u 6 + two length-n contractions accumulated 4n +
+                A(m) du 6 + 1), face item 18, RK update, lift and fused energy 9;
+    shallow water  volume 3 (5 + 12n + 5 + 3), face item 25, update 22."""
     n = N + 1
     per_face = 6.0 * n * n / n ** 3
     if system == "transport":
-        return 3 * (14 + 4 * n) + per_face * 18 + 10
-    return 3 * (16 + 12 * n) + per_face * 25 + 25
+        return 3 * (13 + 4 * n) + per_face * 18 + 9
+    return 3 * (13 + 12 * n) + per_face * 25 + 22
 
 
 def run_friedrichs(args, hbm_peak, peak_kind):

@@ -43,9 +43,10 @@ struct FSys<DGW_SYSTEM_SHALLOW_WATER> {
     out[2] = m2 * w[0];
   }
   static __device__ __forceinline__ void S(const double*, double m1, double m2, double, const double* d, double* out) {
-    const double nu = sqrt(m1 * m1 + m2 * m2);
-    const double tq = nu > 0.0 ? (m1 * d[1] + m2 * d[2]) / nu : 0.0;
-    out[0] = nu * d[0];
+    const double mm = m1 * m1 + m2 * m2;
+    const double inu = mm > 0.0 ? rsqrt(mm) : 0.0;
+    const double tq = (m1 * d[1] + m2 * d[2]) * inu;
+    out[0] = mm * inu * d[0];
     out[1] = m1 * tq;
     out[2] = m2 * tq;
   }
@@ -126,22 +127,22 @@ __global__ void __launch_bounds__(Shape<N>::NT) friedrichs_stage_kernel(const St
       const int stride = dir == 0 ? 1 : (dir == 1 ? n : nf);
       const int a = dir == 0 ? ix : (dir == 1 ? iy : iz);
       const int base = t - a * stride;
-      double cs[M], ds[M];
+      double ds[M];
 #pragma unroll
-      for (int q = 0; q < M; ++q) cs[q] = ds[q] = 0.0;
+      for (int q = 0; q < M; ++q) ds[q] = 0.0;
 #pragma unroll
       for (int b = 0; b < n; ++b) {
         const double Dab = D_s[a * n + b];
 #pragma unroll
         for (int q = 0; q < M; ++q) {
-          cs[q] += Dab * f_s[q * NTILE + base + b * stride];
+          acc[q] += Dab * f_s[q * NTILE + base + b * stride];
           ds[q] += Dab * u_s[q * NTILE + base + b * stride];
         }
       }
       double G[M];
       Y::A(p.beta, m1, m2, m3, ds, G);
 #pragma unroll
-      for (int q = 0; q < M; ++q) acc[q] += cs[q] + G[q];
+      for (int q = 0; q < M; ++q) acc[q] += G[q];
     }
     __syncthreads();
   }
@@ -190,7 +191,7 @@ __global__ void __launch_bounds__(Shape<N>::NT) friedrichs_stage_kernel(const St
     double Ad[M], Sd[M];
     Y::A(p.beta, m1, m2, m3, du, Ad);
     Y::S(p.beta, m1, m2, m3, du, Sd);
-    const double s = 0.5 * p.w_end_inv * jv;
+    const double s = 0.5 * p.w_end_inv * jv * (LSRK ? p.dt : 1.0);   // LSRK: dt L(u) directly
 #pragma unroll
     for (int q = 0; q < M; ++q) x_s[q * NFI + it] = s * (Ad[q] - p.tau * Sd[q]);
   }
@@ -199,7 +200,7 @@ __global__ void __launch_bounds__(Shape<N>::NT) friedrichs_stage_kernel(const St
   double e_node = 0.0;
   if (active) {
     double r[M];
-    const double hv = -0.5 * g_s[9 * NTILE + t];
+    const double hv = -0.5 * g_s[9 * NTILE + t] * (LSRK ? p.dt : 1.0);
 #pragma unroll
     for (int q = 0; q < M; ++q) r[q] = hv * acc[q];
     const int fb0 = el * 6 * nf;
@@ -220,7 +221,7 @@ __global__ void __launch_bounds__(Shape<N>::NT) friedrichs_stage_kernel(const St
       const bool first = p.first != 0;
 #pragma unroll
       for (int q = 0; q < M; ++q) {
-        const double dtr = p.dt * r[q];
+        const double dtr = r[q];                       // dt already applied
         const double rn = first ? dtr : fma(p.a, p.res[q * fstride + gidx], dtr);
         p.res[q * fstride + gidx] = rn;
         const double uo = fma(p.b, rn, u_s[q * NTILE + t]);

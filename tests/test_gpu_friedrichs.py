@@ -58,10 +58,12 @@ def _dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-@pytest.mark.parametrize("system,N,E", [("transport", 1, 3), ("transport", 3, 3), ("transport", 4, 2),
-                                        ("transport", 7, 2), ("shallow_water", 2, (4, 3, 1)),
-                                        ("shallow_water", 3, (3, 3, 2)), ("shallow_water", 4, (3, 2, 1)),
-                                        ("shallow_water", 7, (2, 2, 1))])
+@pytest.mark.parametrize("system,N,E", [("transport", 1, 3), ("transport", 2, 3), ("transport", 3, 3),
+                                        ("transport", 4, 2), ("transport", 5, 2), ("transport", 6, 2),
+                                        ("transport", 7, 2), ("shallow_water", 1, (5, 3, 1)),
+                                        ("shallow_water", 2, (4, 3, 1)), ("shallow_water", 3, (3, 3, 2)),
+                                        ("shallow_water", 4, (3, 2, 1)), ("shallow_water", 5, (2, 2, 1)),
+                                        ("shallow_water", 6, (2, 2, 1)), ("shallow_water", 7, (2, 2, 1))])
 @pytest.mark.parametrize("tau", [0, 1])
 def test_rhs_parity(system, N, E, tau):
     import torch
