@@ -165,3 +165,26 @@ def test_refusals():
     assert capi.dgw_batch_set(hb, 1, P(sw._ctx.value), P(z.data_ptr()), P(z.clone().data_ptr()), D(0.01), D(0.0),
                               None) == -7
     capi.dgw_batch_destroy(hb)
+
+
+@pytest.mark.parametrize("system,E", [("transport", 3), ("shallow_water", (4, 3, 1))])
+def test_host_pointer_paths_match_device_paths(system, E):
+    """rhs, step and energy on host (numpy) buffers stage through the context's
+    device buffers, sized for m fields; they must equal the device-pointer calls."""
+    import torch
+    c = FCase(system, E, 2, rotate=3, seed=9)
+    u_h = np.ascontiguousarray(c.u0)
+    out_h = np.zeros_like(u_h)
+    c.solver.rhs(u_h, out_h)
+    ud = _dev(u_h)
+    out_d = torch.empty_like(ud)
+    c.solver.rhs(ud, out_d)
+    assert np.array_equal(out_h, out_d.cpu().numpy())
+    dt = c.solver.dt_cfl()
+    res_h = np.zeros_like(u_h)
+    u_step = u_h.copy()
+    c.solver.step(u_step, res_h, dt, 3)
+    res_d = torch.zeros_like(ud)
+    c.solver.step(ud, res_d, dt, 3)
+    assert np.array_equal(u_step, ud.cpu().numpy()) and np.array_equal(res_h, res_d.cpu().numpy())
+    assert c.solver.energy(u_step) == c.solver.energy(ud)
