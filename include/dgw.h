@@ -175,7 +175,8 @@ dgw_status dgw_energy(dgw_ctx* ctx, const double* u, double* energy_out, void* s
  * that element at the stage times t + c_s dt of dgw_rhs/dgw_stage/dgw_step
  * (whose t arguments are the step start times).  element = -1 removes the
  * source.  DGW_ERR_STATE before mesh and material (material sets rho of the
- * source element: upload material first, set the source after). */
+ * source element: upload material first, set the source after).  Elastic
+ * contexts only (DGW_ERR_UNSUPPORTED otherwise). */
 dgw_status dgw_source_set(dgw_ctx* ctx, int64_t element, const double* xi, const double* force, double f0,
                           double t0);
 
@@ -191,12 +192,13 @@ dgw_status dgw_source_set(dgw_ctx* ctx, int64_t element, const double* xi, const
  * with A_k -> -A_k (the upwind stabilisation of eq. RiemannFluxBoth is
  * symmetric and unchanged).  Stage inputs are recomputed from u_ckpt.  Adjoint
  * sources between steps (dgw_receivers_adjoint) need nsteps = 1 per call.
- * FP64 contexts only (DGW_ERR_UNSUPPORTED otherwise). */
+ * Elastic FP64 contexts only (DGW_ERR_UNSUPPORTED otherwise). */
 dgw_status dgw_adjoint_step(dgw_ctx* ctx, double* lam_u, double* lam_res, double* grad_mat, const double* u_ckpt,
                             double t0, double dt, int nsteps, void* stream);
 
 /* Receivers: velocity sampled at reference points xi[n][3] of elements[n]
- * (host arrays) with the element's Lagrange basis.  n = 0 removes them. */
+ * (host arrays) with the element's Lagrange basis.  n = 0 removes them.
+ * Elastic contexts only (DGW_ERR_UNSUPPORTED otherwise). */
 dgw_status dgw_receivers_set(dgw_ctx* ctx, int n, const int64_t* elements, const double* xi);
 
 /* out[n][3] (device) = velocity of u (device) at the receivers. */
