@@ -290,8 +290,9 @@ dgw_status dgw_energy_static(int N, int64_t nel, const double* x, const double* 
  * with b = u^m/dt + f is one implicit Euler step solved element by element
  * (Section 3.3, the locally implicit method).  Shallow water: sigma = 2/dt
  * with b = sigma u^m + L(u^m) (f = dgw_rhs of u^m) is one Crank-Nicolson
- * step (Section 6.3).  Degrees: transport N <= 4, shallow water N <= 2 (the
- * local block of m Np rows is inverted in shared memory). */
+ * step (Section 6.3).  Degrees: transport N <= 4, shallow water N <= 3; the
+ * local block of m Np rows is inverted in shared memory up to 125 rows and in
+ * global memory beyond (shallow water N = 3). */
 
 /* Build and invert sigma I - L_K^self for every element (device memory:
  * nel * (m Np)^2 doubles, about 1 MB per 8 elements for transport at N = 4).

@@ -27,10 +27,14 @@
 namespace dgw {
 namespace {
 
-// Degrees built: the local block has m Np rows and must fit shared memory
-// (transport N = 4: 125 x 125, 122 KB; shallow water N = 2: 81 x 81).
+// Degrees built: transport N <= 4, shallow water N <= 3.  A local block of
+// m Np rows is inverted in shared memory up to 125 x 125 (122 KB) and in its
+// own global-memory block beyond (shallow water N = 3: 192 rows, 295 KB; the
+// blocks of the CTAs in flight stay in L2).  Shallow water at N = 4 (375 rows,
+// 1.1 MB per block) would stream every block through HBM once per pivot.
 constexpr int kIhdgMaxNTransport = 4;
-constexpr int kIhdgMaxNShallow = 2;
+constexpr int kIhdgMaxNShallow = 3;
+constexpr int kIhdgSmemRows = 125;
 
 // Unit vector of (field q, node j) in every element of an [m][nel][Np] state.
 __global__ void unit_column_kernel(double* u, long long nodes, int Np, int m, int q, int j) {
@@ -58,19 +62,23 @@ __global__ void scatter_column_kernel(const double* col, double* A, long long no
 
 // In-place Gauss-Jordan inversion of each n x n block of A (partial pivoting;
 // row exchanges recorded and undone as column exchanges at the end), written
-// back transposed.  A zero pivot sets *singular.
+// back transposed.  SMEM: the block is worked on in shared memory, else in
+// place in global memory.  A zero pivot sets *singular.
+template <bool SMEM>
 __global__ void __launch_bounds__(256) gj_invert_kernel(double* A, int n, long long nel, int* singular) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* a = reinterpret_cast<double*>(smem_raw);          // [n][n]
-  double* fcol = a + n * n;                                  // [n]
-  int* perm = reinterpret_cast<int*>(fcol + n);              // [n]
-  __shared__ int piv_row;
-  __shared__ double pinv;
   const long long e = blockIdx.x;
   if (e >= nel) return;
   double* Ae = A + static_cast<size_t>(e) * n * n;
+  double* a = SMEM ? reinterpret_cast<double*>(smem_raw) : Ae;                  // [n][n]
+  double* fcol = reinterpret_cast<double*>(smem_raw) + (SMEM ? n * n : 0);     // [n]
+  int* perm = reinterpret_cast<int*>(fcol + n);                                 // [n]
+  __shared__ int piv_row;
+  __shared__ double pinv;
   const int t = threadIdx.x, NT = blockDim.x;
-  for (int q = t; q < n * n; q += NT) a[q] = Ae[q];
+  if constexpr (SMEM) {
+    for (int q = t; q < n * n; q += NT) a[q] = Ae[q];
+  }
   __syncthreads();
   for (int k = 0; k < n; ++k) {
     if (t < 32) {
@@ -130,9 +138,20 @@ __global__ void __launch_bounds__(256) gj_invert_kernel(double* A, int n, long l
     }
     __syncthreads();
   }
-  for (int q = t; q < n * n; q += NT) {
-    const int i = q / n, j = q - (q / n) * n;
-    Ae[j * n + i] = a[q];
+  if constexpr (SMEM) {
+    for (int q = t; q < n * n; q += NT) {
+      const int i = q / n, j = q - (q / n) * n;
+      Ae[j * n + i] = a[q];
+    }
+  } else {
+    for (int q = t; q < n * n; q += NT) {            // transpose in place, each pair once
+      const int i = q / n, j = q - (q / n) * n;
+      if (i < j) {
+        const double tmp = a[i * n + j];
+        a[i * n + j] = a[j * n + i];
+        a[j * n + i] = tmp;
+      }
+    }
   }
 }
 
@@ -264,6 +283,7 @@ cudaError_t launch_iter_any(const dgw_ctx* c, const double* u_prev, const double
     switch (c->cfg.N) {
       case 1: return launch_iter<1, 3>(c, u_prev, f, uk, unext, s);
       case 2: return launch_iter<2, 3>(c, u_prev, f, uk, unext, s);
+      case 3: return launch_iter<3, 3>(c, u_prev, f, uk, unext, s);
       default: return cudaErrorInvalidValue;
     }
   }
@@ -289,6 +309,7 @@ cudaError_t launch_face_coef(const dgw_ctx* c, cudaStream_t s) {
     face_coef_kernel<NN, MM><<<blocks, 256, 0, s>>>(geo, c->vmapP, c->nel, b[0], b[1], b[2], tau, wi, c->ihdg_cf); \
     break;
     DGW_FC(1, 1, 2) DGW_FC(2, 1, 4) DGW_FC(3, 1, 6) DGW_FC(4, 1, 8) DGW_FC(1, 3, 3) DGW_FC(2, 3, 5)
+    DGW_FC(3, 3, 7)
 #undef DGW_FC
     default:
       return cudaErrorInvalidValue;
@@ -343,7 +364,7 @@ dgw_status dgw_ihdg_setup(dgw_ctx* c, double sigma, void* stream) {
   if (c->cfg.system == DGW_SYSTEM_TRANSPORT && c->cfg.N > dgw::kIhdgMaxNTransport)
     return dgw::ifail(c, DGW_ERR_UNSUPPORTED, "iHDG-II for transport is built for N <= 4");
   if (c->cfg.system == DGW_SYSTEM_SHALLOW_WATER && c->cfg.N > dgw::kIhdgMaxNShallow)
-    return dgw::ifail(c, DGW_ERR_UNSUPPORTED, "iHDG-II for shallow water is built for N <= 2");
+    return dgw::ifail(c, DGW_ERR_UNSUPPORTED, "iHDG-II for shallow water is built for N <= 3");
   if (!c->has_mesh) return dgw::ifail(c, DGW_ERR_STATE, "iHDG-II set-up before the mesh");
   if (!(sigma >= 0.0) || !std::isfinite(sigma)) return dgw::ifail(c, DGW_ERR_ARG, "sigma must be finite and >= 0");
   if (cudaSetDevice(c->device) != cudaSuccess) return dgw::ifail(c, DGW_ERR_CUDA, "cudaSetDevice");
@@ -392,10 +413,15 @@ dgw_status dgw_ihdg_setup(dgw_ctx* c, double sigma, void* stream) {
     cudaFree(singular);
     return dgw::ifail(c, DGW_ERR_CUDA, std::string("local matrices: ") + cudaGetErrorString(e));
   }
-  const size_t smem = static_cast<size_t>(nb) * nb * 8 + nb * 8 + nb * 4;
-  e = cudaFuncSetAttribute(dgw::gj_invert_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess) {
-    dgw::gj_invert_kernel<<<(unsigned)nel, 256, smem, s>>>(c->ihdg_inv, nb, nel, singular);
+  if (nb <= dgw::kIhdgSmemRows) {
+    const size_t smem = static_cast<size_t>(nb) * nb * 8 + nb * 8 + nb * 4;
+    e = cudaFuncSetAttribute(dgw::gj_invert_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) {
+      dgw::gj_invert_kernel<true><<<(unsigned)nel, 256, smem, s>>>(c->ihdg_inv, nb, nel, singular);
+      e = cudaGetLastError();
+    }
+  } else {
+    dgw::gj_invert_kernel<false><<<(unsigned)nel, 256, nb * 8 + nb * 4, s>>>(c->ihdg_inv, nb, nel, singular);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = dgw::launch_face_coef(c, s);

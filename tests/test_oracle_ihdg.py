@@ -147,7 +147,7 @@ def test_shallow_water_cn_step_converges_to_the_direct_step():
     assert ih.norm(ud - wl.shallow_water_standing_wave(x, 0.1)) < 0.05 * ih.norm(ud)
 
 
-@pytest.mark.parametrize("E,N", [(4, 1), (8, 1), (16, 1), (4, 2), (8, 2)])
+@pytest.mark.parametrize("E,N", [(4, 1), (8, 1), (16, 1), (4, 2), (8, 2), (4, 3)])
 def test_shallow_water_iteration_counts_of_the_paper(E, N):
     """The paper's iHDG-II counts (golden table), with eq. tolerancecriteriarelerror
     on the first Crank-Nicolson step: within 3 for both time steps; more
