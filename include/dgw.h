@@ -281,7 +281,8 @@ dgw_status dgw_energy_static(int N, int64_t nel, const double* x, const double* 
 /* ---- iHDG-II: the paper's locally implicit iteration ---------------------
  * The paper's iHDG-II algorithm (Section 3, Algorithm "The iHDG-II
  * approach"; eqs. iHDGlocal and iHDGtrace) for sigma u - L(u) = b with L the
- * upwind operator of a transport or shallow-water context: every element
+ * upwind operator of the context (transport, shallow water, or the FP64
+ * elastic operator without its point force): every element
  * solves its local problem with its own unknowns at iteration k+1 and its
  * neighbours' at k in the weighted trace,
  *     (sigma I - L_K^self) u_K^{k+1} = b_K + L_K^nbr(u^k),
@@ -290,16 +291,22 @@ dgw_status dgw_energy_static(int N, int64_t nel, const double* x, const double* 
  * with b = u^m/dt + f is one implicit Euler step solved element by element
  * (Section 3.3, the locally implicit method).  Shallow water: sigma = 2/dt
  * with b = sigma u^m + L(u^m) (f = dgw_rhs of u^m) is one Crank-Nicolson
- * step (Section 6.3).  Degrees: transport N <= 4, shallow water N <= 3; the
- * local block of m Np rows is inverted in shared memory up to 125 rows and in
- * global memory beyond (shallow water N = 3). */
+ * step (Section 6.3).  Elastic (FP64 contexts): sigma = 1/dt with
+ * b = u^m/dt + f is one implicit Euler step, sigma = 2/dt with
+ * b = sigma u^m + L(u^m) one Crank-Nicolson step, of du/dt = L(u) (L includes
+ * Q^{-1}); a point force enters through f.  Degrees: transport N <= 4, shallow
+ * water N <= 3, elastic N <= 3; the local block of m Np rows is inverted in
+ * shared memory up to 125 rows and in global memory beyond. */
 
 /* Build and invert sigma I - L_K^self for every element (device memory:
  * nel * (m Np)^2 doubles, about 1 MB per 8 elements for transport at N = 4).
- * sigma >= 0.  DGW_ERR_UNSUPPORTED for elastic contexts and beyond the degrees
- * above;
- * DGW_ERR_STATE before the mesh; DGW_ERR_ARG if a local matrix is
- * singular.  Synchronises `stream`. */
+ * sigma >= 0.  Elastic: nel * (9 Np)^2 doubles (2.65 MB per element at
+ * N = 3); the local blocks are formed by applying the operator to unit vectors
+ * in the elements of one colour of a greedy element colouring at a time.
+ * DGW_ERR_UNSUPPORTED for mixed-precision contexts, beyond the degrees above,
+ * and (elastic) for a mesh where an element is its own neighbour;
+ * DGW_ERR_STATE before the mesh (elastic: before the material); DGW_ERR_ARG if
+ * a local matrix is singular.  Synchronises `stream`. */
 dgw_status dgw_ihdg_setup(dgw_ctx* ctx, double sigma, void* stream);
 
 /* Iterate from the initial guess in u (device [m][nel][Np], overwritten with

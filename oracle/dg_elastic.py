@@ -282,6 +282,8 @@ class ElasticDG:
         self.lam = np.asarray(lam, dtype=np.float64)
         self.mu = np.asarray(mu, dtype=np.float64)
         self.tau = float(tau)
+        self.m = NFIELD
+        self.self_only = False      # True: interior neighbour states taken as zero (L_K^self)
         self.face_nodes = [face_node_indices(f, self.N) for f in range(6)]
         wv = np.einsum("k,j,i->kji", self.w, self.w, self.w).ravel()
         self.w_vol = wv                                        # [Np]
@@ -393,7 +395,8 @@ class ElasticDG:
             raise ValueError(f"face {f}: element without neighbour and without boundary tag")
         flat = u.reshape(NFIELD, -1)
         up = np.zeros_like(um)
-        up[:, interior] = flat[:, nbr[interior]]
+        if not self.self_only:
+            up[:, interior] = flat[:, nbr[interior]]
         free = tag == 1           # traction-free: keep the velocity, mirror the stress
         up[:3, free] = um[:3, free]
         up[3:, free] = -um[3:, free]

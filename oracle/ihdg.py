@@ -64,7 +64,7 @@ class IHDG:
                 for j in range(self.Np):
                     u = np.zeros((self.m, self.nel, self.Np))
                     u[q, :, j] = 1.0
-                    self.Lself[:, :, q * self.Np + j] = np.moveaxis(op.rhs(u), 0, 1).reshape(self.nel, n)
+                    self.Lself[:, :, q * self.Np + j] = np.moveaxis(op.rhs(u, source=False), 0, 1).reshape(self.nel, n)
         finally:
             op.self_only = False
         self.local = self.sigma * np.eye(n)[None] - self.Lself      # sigma I - L_K^self
@@ -77,7 +77,7 @@ class IHDG:
 
     def neighbour_term(self, u):
         """L_K^nbr(u) = L(u)_K - L_K^self u_K for every element: [m, nel, Np]."""
-        return self.op.rhs(u) - self._unflat(np.einsum("eij,ej->ei", self.Lself, self._flat(u)))
+        return self.op.rhs(u, source=False) - self._unflat(np.einsum("eij,ej->ei", self.Lself, self._flat(u)))
 
     def iterate(self, b, u):
         """One iHDG-II iteration from u^k: the local solves of every element."""
@@ -113,7 +113,7 @@ class IHDG:
         for j in range(n):
             e = np.zeros(n)
             e[j] = 1.0
-            A[:, j] = self.sigma * e - self.op.rhs(e.reshape(self.m, self.nel, self.Np)).ravel()
+            A[:, j] = self.sigma * e - self.op.rhs(e.reshape(self.m, self.nel, self.Np), source=False).ravel()
         return np.linalg.solve(A, b.ravel()).reshape(b.shape)
 
 

@@ -34,20 +34,27 @@ namespace {
 // 1.1 MB per block) would stream every block through HBM once per pivot.
 constexpr int kIhdgMaxNTransport = 4;
 constexpr int kIhdgMaxNShallow = 3;
+constexpr int kIhdgMaxNElastic = 3;     // 9 Np = 576 rows at N = 3 (2.65 MB per block)
 constexpr int kIhdgSmemRows = 125;
 
-// Unit vector of (field q, node j) in every element of an [m][nel][Np] state.
-__global__ void unit_column_kernel(double* u, long long nodes, int Np, int m, int q, int j) {
+// Unit vector of (field q, node j) in every element of an [m][nel][Np] state
+// (color == nullptr), or in the elements whose colour is `colour`.
+__global__ void unit_column_kernel(double* u, long long nodes, int Np, int m, int q, int j, const int* color,
+                                   int colour) {
   const long long total = nodes * m;
   for (long long g = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; g < total;
-       g += static_cast<long long>(gridDim.x) * blockDim.x)
-    u[g] = (g / nodes == q && (g % nodes) % Np == j) ? 1.0 : 0.0;
+       g += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long rem = g % nodes;
+    const bool mine = color == nullptr || color[rem / Np] == colour;
+    u[g] = (g / nodes == q && rem % Np == j && mine) ? 1.0 : 0.0;
+  }
 }
 
-// Column (q, j) of every block: A[e][(p, i)][(q, j)] = sigma delta - col[p][e][i]
-// (row-major blocks of n = m Np, rows and columns field-major).
+// Column (q, j) of every block (color == nullptr) or of the blocks of colour
+// `colour`: A[e][(p, i)][(q, j)] = sigma delta - col[p][e][i] (row-major
+// blocks of n = m Np, rows and columns field-major).
 __global__ void scatter_column_kernel(const double* col, double* A, long long nodes, int Np, int m, int qj,
-                                      double sigma) {
+                                      double sigma, const int* color, int colour) {
   const int n = m * Np;
   const long long total = nodes * m;
   for (long long g = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; g < total;
@@ -55,6 +62,7 @@ __global__ void scatter_column_kernel(const double* col, double* A, long long no
     const int p = static_cast<int>(g / nodes);
     const long long rem = g - static_cast<long long>(p) * nodes;
     const long long e = rem / Np;
+    if (color != nullptr && color[e] != colour) continue;
     const int row = p * Np + static_cast<int>(rem - e * Np);
     A[(e * n + row) * n + qj] = (row == qj ? sigma : 0.0) - col[g];
   }
@@ -296,6 +304,114 @@ cudaError_t launch_iter_any(const dgw_ctx* c, const double* u_prev, const double
   }
 }
 
+// One iHDG-II iteration in residual form (the elastic system): with
+// r = sigma u_prev + f + L(u^k) - sigma u^k, u^{k+1}_K = u^k_K + inv_K r_K.  As
+// L(u)_K = L_K^self u^k_K + L_K^nbr(u^k), r_K = b_K + L_K^nbr(u^k) - (sigma I -
+// L_K^self) u^k_K, so this is the local solve of eq. iHDGlocal; the neighbour
+// terms come from the full operator (Lu = L(u^k)) instead of per-face
+// coefficients.  part[e] = sum_(p,i) w J (u^{k+1} - u^k)^2 over the element.
+template <int N, int M>
+__global__ void __launch_bounds__((M * (N + 1) * (N + 1) * (N + 1) + 31) / 32 * 32)
+    ihdg_resid_kernel(const double* __restrict__ invT, const double* __restrict__ Lu, const double* __restrict__ wJ,
+                      const double* u_prev, const double* f, double sigma, const double* __restrict__ uk,
+                      double* __restrict__ unext, long long nel, double* part) {
+  constexpr int n = N + 1, Np = n * n * n, NB = M * Np, NT = (NB + 31) / 32 * 32;
+  __shared__ double r_s[NB];
+  __shared__ double red[32];
+  const long long e = blockIdx.x;
+  const int t = threadIdx.x;
+  const size_t fstride = static_cast<size_t>(nel) * Np;
+  const int p = t / Np, i = t - (t / Np) * Np;
+  const size_t gi = p * fstride + static_cast<size_t>(e) * Np + i;
+  double ukv = 0.0;
+  if (t < NB) {
+    ukv = uk[gi];
+    r_s[t] = (u_prev ? sigma * u_prev[gi] : 0.0) + (f ? f[gi] : 0.0) + Lu[gi] - sigma * ukv;
+  }
+  __syncthreads();
+  double v = 0.0;
+  if (t < NB) {
+    const double* Mt = invT + static_cast<size_t>(e) * NB * NB + t;
+    double acc = 0.0;
+#pragma unroll 3
+    for (int j = 0; j < NB; ++j) acc = fma(Mt[static_cast<size_t>(j) * NB], r_s[j], acc);
+    const double un = ukv + acc;
+    unext[gi] = un;
+    const double d = un - ukv;
+    v = wJ[static_cast<size_t>(e) * Np + i] * d * d;
+  }
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  if ((t & 31) == 0) red[t >> 5] = v;
+  __syncthreads();
+  if (t == 0) {
+    double sum = 0.0;
+    for (int w = 0; w < NT / 32; ++w) sum += red[w];
+    part[e] = sum;
+  }
+}
+
+cudaError_t launch_resid_any(const dgw_ctx* c, const double* u_prev, const double* f, const double* uk,
+                             const double* Lu, double* unext, cudaStream_t s) {
+  switch (c->cfg.N) {
+#define DGW_RCASE(NN)                                                                                          \
+  case NN: {                                                                                                   \
+    constexpr int NT = (9 * (NN + 1) * (NN + 1) * (NN + 1) + 31) / 32 * 32;                                    \
+    ihdg_resid_kernel<NN, 9><<<(unsigned)c->nel, NT, 0, s>>>(c->ihdg_inv, Lu, c->wJ, u_prev, f, c->ihdg_sigma, uk, \
+                                                              unext, c->nel, c->ihdg_part);                    \
+    return cudaGetLastError();                                                                                 \
+  }
+    DGW_RCASE(1) DGW_RCASE(2) DGW_RCASE(3)
+#undef DGW_RCASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+// L(u) of an FP64 elastic context without the point force (the operator of
+// sigma u - L(u) = b; a source enters through f).
+cudaError_t launch_elastic_operator(const dgw_ctx* c, const double* u, double* out, cudaStream_t s) {
+  StageParams p{};
+  int epb = 0, nthreads = 0;
+  stage_shape(c->cfg.N, &epb, &nthreads);
+  p.pf_elems = 2LL * c->sm_count * epb;
+  p.src_elem = -1;
+  p.u_in = u;
+  p.out = out;
+  p.geo = c->geo;
+  p.fz = c->fz;
+  p.vmapP = c->vmapP;
+  p.mat = c->mat;
+  p.nel = c->nel;
+  p.tau = c->cfg.flux_tau ? 1.0 : 0.0;
+  p.w_end_inv = 1.0 / c->ref.w[0];
+  for (int i = 0; i < (c->cfg.N + 1) * (c->cfg.N + 1); ++i) p.D[i] = c->ref.D[i];
+  return launch_stage_fp64(c->cfg.N, false, p, s);
+}
+
+// Greedy colouring of the element graph (elements sharing an interior face get
+// different colours).  Returns the number of colours, or -1 if an element is its
+// own neighbour (no colouring then separates its own values from its neighbour's).
+int color_elements(const dgw_ctx* c, std::vector<int>& color) {
+  const long long nel = c->nel;
+  color.assign(static_cast<size_t>(nel), -1);
+  int ncol = 0;
+  for (long long e = 0; e < nel; ++e) {
+    unsigned long long used = 0;
+    for (int f = 0; f < 6; ++f) {
+      const size_t k = static_cast<size_t>(e) * 6 + f;
+      const long long nb = c->etoe[k];
+      if (nb < 0 || c->bc[k] != DGW_BC_INTERIOR) continue;
+      if (nb == e) return -1;
+      if (color[nb] >= 0 && color[nb] < 64) used |= 1ull << color[nb];
+    }
+    int col = 0;
+    while (col < 64 && ((used >> col) & 1ull)) ++col;
+    color[e] = col;
+    if (col + 1 > ncol) ncol = col + 1;
+  }
+  return ncol;
+}
+
 cudaError_t launch_face_coef(const dgw_ctx* c, cudaStream_t s) {
   const double* geo = static_cast<const double*>(c->geo);
   const double tau = c->cfg.flux_tau ? 1.0 : 0.0;
@@ -359,13 +475,24 @@ extern "C" {
 
 dgw_status dgw_ihdg_setup(dgw_ctx* c, double sigma, void* stream) {
   if (!c) return dgw::ifail(nullptr, DGW_ERR_ARG, "null context");
-  if (c->cfg.system == DGW_SYSTEM_ELASTIC)
-    return dgw::ifail(c, DGW_ERR_UNSUPPORTED, "iHDG-II is built for transport and shallow water");
+  const bool elastic = c->cfg.system == DGW_SYSTEM_ELASTIC;
+  if (elastic && c->cfg.precision != DGW_PRECISION_FP64)
+    return dgw::ifail(c, DGW_ERR_UNSUPPORTED, "iHDG-II for the elastic system is built in FP64 only");
+  if (elastic && c->cfg.N > dgw::kIhdgMaxNElastic)
+    return dgw::ifail(c, DGW_ERR_UNSUPPORTED, "iHDG-II for the elastic system is built for N <= 3");
   if (c->cfg.system == DGW_SYSTEM_TRANSPORT && c->cfg.N > dgw::kIhdgMaxNTransport)
     return dgw::ifail(c, DGW_ERR_UNSUPPORTED, "iHDG-II for transport is built for N <= 4");
   if (c->cfg.system == DGW_SYSTEM_SHALLOW_WATER && c->cfg.N > dgw::kIhdgMaxNShallow)
     return dgw::ifail(c, DGW_ERR_UNSUPPORTED, "iHDG-II for shallow water is built for N <= 3");
   if (!c->has_mesh) return dgw::ifail(c, DGW_ERR_STATE, "iHDG-II set-up before the mesh");
+  if (elastic && !c->has_material) return dgw::ifail(c, DGW_ERR_STATE, "iHDG-II set-up before the material");
+  std::vector<int> color;
+  int ncolors = 0;
+  if (elastic) {
+    ncolors = dgw::color_elements(c, color);
+    if (ncolors < 0)
+      return dgw::ifail(c, DGW_ERR_UNSUPPORTED, "iHDG-II for the elastic system: an element is its own neighbour");
+  }
   if (!(sigma >= 0.0) || !std::isfinite(sigma)) return dgw::ifail(c, DGW_ERR_ARG, "sigma must be finite and >= 0");
   if (cudaSetDevice(c->device) != cudaSuccess) return dgw::ifail(c, DGW_ERR_CUDA, "cudaSetDevice");
   cudaStream_t s = (cudaStream_t)stream;
@@ -375,7 +502,8 @@ dgw_status dgw_ihdg_setup(dgw_ctx* c, double sigma, void* stream) {
   dgw::ihdg_free(c);
   const size_t inv_bytes = static_cast<size_t>(nel) * nb * nb * sizeof(double);
   if (cudaMalloc(&c->ihdg_inv, inv_bytes) != cudaSuccess ||
-      cudaMalloc(&c->ihdg_cf, static_cast<size_t>(nel) * 6 * nf * m * m * sizeof(double)) != cudaSuccess ||
+      (!elastic &&
+       cudaMalloc(&c->ihdg_cf, static_cast<size_t>(nel) * 6 * nf * m * m * sizeof(double)) != cudaSuccess) ||
       cudaMalloc(&c->ihdg_part, (static_cast<size_t>(nel) + 1 + dgw::kEnergyBlocks) * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&c->ihdg_u2, nodes * m * sizeof(double)) != cudaSuccess) {
     dgw::ihdg_free(c);
@@ -399,13 +527,41 @@ dgw_status dgw_ihdg_setup(dgw_ctx* c, double sigma, void* stream) {
   for (int i = 0; i < n * n; ++i) p.D[i] = c->ref.D[i];
   const int blocks = 4 * c->sm_count;
   cudaError_t e = cudaSuccess;
-  for (int qj = 0; qj < nb && e == cudaSuccess; ++qj) {
-    dgw::unit_column_kernel<<<blocks, 256, 0, s>>>(c->ihdg_u2, static_cast<long long>(nodes), Np, m, qj / Np, qj % Np);
+  if (elastic) {
+    // The elastic operator has no self-only mode: apply it to the unit vector of
+    // (field, node) in the elements of one colour at a time.  Their interior
+    // neighbours are of other colours, hence zero, and L(u)_K = L_K^self u_K there.
+    int* color_d = nullptr;
+    e = cudaMalloc(&color_d, color.size() * sizeof(int));
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(color_d, color.data(), color.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+    for (int col = 0; col < ncolors && e == cudaSuccess; ++col) {
+      for (int qj = 0; qj < nb && e == cudaSuccess; ++qj) {
+        dgw::unit_column_kernel<<<blocks, 256, 0, s>>>(c->ihdg_u2, static_cast<long long>(nodes), Np, m, qj / Np,
+                                                        qj % Np, color_d, col);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = dgw::launch_elastic_operator(c, c->ihdg_u2, c->u2, s);
+        if (e == cudaSuccess) {
+          dgw::scatter_column_kernel<<<blocks, 256, 0, s>>>(c->u2, c->ihdg_inv, static_cast<long long>(nodes), Np, m,
+                                                             qj, sigma, color_d, col);
+          e = cudaGetLastError();
+        }
+      }
+    }
+    if (color_d) {
+      const cudaError_t e2 = cudaStreamSynchronize(s);
+      if (e == cudaSuccess) e = e2;
+      cudaFree(color_d);
+    }
+  }
+  for (int qj = 0; qj < nb && e == cudaSuccess && !elastic; ++qj) {
+    dgw::unit_column_kernel<<<blocks, 256, 0, s>>>(c->ihdg_u2, static_cast<long long>(nodes), Np, m, qj / Np, qj % Np,
+                                                    nullptr, 0);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = dgw::launch_friedrichs(c->cfg.system, N, false, p, s);
     if (e == cudaSuccess) {
       dgw::scatter_column_kernel<<<blocks, 256, 0, s>>>(c->u2, c->ihdg_inv, static_cast<long long>(nodes), Np, m, qj,
-                                                         sigma);
+                                                         sigma, nullptr, 0);
       e = cudaGetLastError();
     }
   }
@@ -424,7 +580,7 @@ dgw_status dgw_ihdg_setup(dgw_ctx* c, double sigma, void* stream) {
     dgw::gj_invert_kernel<false><<<(unsigned)nel, 256, nb * 8 + nb * 4, s>>>(c->ihdg_inv, nb, nel, singular);
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess) e = dgw::launch_face_coef(c, s);
+  if (e == cudaSuccess && !elastic) e = dgw::launch_face_coef(c, s);
   int sing = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&sing, singular, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -457,7 +613,12 @@ dgw_status dgw_ihdg_solve(dgw_ctx* c, const double* u_prev, const double* f, dou
   double change = INFINITY;
   int k = 0;
   while (k < max_iter) {
-    ICUDA(dgw::launch_iter_any(c, u_prev, f, cur, nxt, s), "iteration kernel");
+    if (c->cfg.system == DGW_SYSTEM_ELASTIC) {
+      ICUDA(dgw::launch_elastic_operator(c, cur, c->u2, s), "operator");
+      ICUDA(dgw::launch_resid_any(c, u_prev, f, cur, c->u2, nxt, s), "iteration kernel");
+    } else {
+      ICUDA(dgw::launch_iter_any(c, u_prev, f, cur, nxt, s), "iteration kernel");
+    }
     ICUDA(dgw::launch_energy_final(c->ihdg_part, static_cast<int>(c->nel), result + 1, result, s), "change norm");
     double half_sq = 0.0;
     ICUDA(cudaMemcpyAsync(&half_sq, result, sizeof(double), cudaMemcpyDeviceToHost, s), "copy change");

@@ -154,11 +154,12 @@ class Solver:
         return val
 
     def ihdg_setup(self, sigma: float, stream=None):
-        """iHDG-II (transport, N <= 4): build and invert sigma I - L_K^self per element."""
+        """iHDG-II: build and invert sigma I - L_K^self per element (transport N <= 4,
+        shallow water N <= 3, FP64 elastic N <= 3)."""
         self._check(capi.dgw_ihdg_setup(self._ctx, float(sigma), _stream_handle(stream)))
 
     def ihdg_solve(self, u, u_prev=None, f=None, tol: float = 1e-10, max_iter: int = 1000, stream=None):
-        """Iterate iHDG-II from the guess in u (device [1, nel, Np], overwritten) for
+        """Iterate iHDG-II from the guess in u (device [m, nel, Np], overwritten) for
         sigma u - L(u) = sigma u_prev + f; returns (iterations, last ||u^k - u^{k-1}||)."""
         self._field_check(u, "u")
         for a, name in ((u_prev, "u_prev"), (f, "f")):

@@ -1,5 +1,5 @@
-"""iHDG-II on the GPU (transport) against the oracle's IHDGTransport and the
-paper's results, through the C ABI.
+"""iHDG-II on the GPU (transport, shallow water, elastic) against the oracle's
+IHDG and the paper's results, through the C ABI.
 
 * every iterate equals the oracle's iterate (the local inverses, the
   neighbour coupling and the update): <= 1e-11 relative L2;
@@ -7,7 +7,10 @@ paper's results, through the C ABI.
   iterations, and the paper's stopping criterion stops at 3E - 1, on meshes
   up to the paper's largest 3-D case (16^3, Table of iteration counts);
 * one locally implicit Euler step equals the oracle's direct implicit step;
-* refusals (degree, system, call order).
+* refusals (degree, system, call order);
+* shallow water: iterates, and the counts of the paper's Crank-Nicolson table;
+* elastic (FP64, upwind): iterates, the direct implicit step, the iteration
+  count, and the exact energy identities of implicit Euler and Crank-Nicolson.
 """
 import os
 
@@ -167,7 +170,7 @@ def test_refusals():
     assert st == -2
     assert capi.dgw_ihdg_setup(s2._ctx, -1.0, None) == -1
     el = Solver(2)
-    assert capi.dgw_ihdg_setup(el._ctx, 0.0, None) == -7
+    assert capi.dgw_ihdg_setup(el._ctx, 0.0, None) == -2          # elastic: mesh first
 
 
 # ---- shallow water, Crank-Nicolson (Section 6.3) ------------------------------
@@ -251,3 +254,102 @@ def test_shallow_water_refuses_degrees_above_three():
     from paper_1711_01175_gb300 import capi
     s, _, _, _ = _sw(2, 4, oracle_side=False)
     assert capi.dgw_ihdg_setup(s._ctx, 20.0, None) == -7
+
+
+# ---- the elastic system (FP64, upwind flux) ------------------------------------
+
+
+def _el(E, N, oracle_side=True, seed=3, precision="fp64", periodic=(True, True, False)):
+    from paper_1711_01175_gb300 import Solver, reference_nodes
+    mesh = wl.structured_hex_mesh(E, periodic, {4: wl.BC_FREE_SURFACE, 5: wl.BC_ABSORBING})
+    rho, lam, mu = wl.smooth_random_material(mesh, seed)
+    x_lib = wl.warped_node_coords(mesh, reference_nodes(N)[0], 0.05)
+    s = Solver(N, precision=precision)
+    s.upload_mesh(x_lib, mesh.etoe, mesh.etof, mesh.orient, mesh.bc)
+    s.upload_material(rho, lam, mu)
+    op = None
+    if oracle_side:
+        x_or = wl.warped_node_coords(mesh, oracle.gll(N)[0], 0.05)
+        op = oracle.ElasticDG(N, x_or, mesh.etoe, mesh.etof, mesh.orient, mesh.bc, rho, lam, mu, 1)
+    return s, op, x_lib, mesh
+
+
+@pytest.mark.parametrize("N,E", [(1, (3, 3, 2)), (2, (3, 2, 2)), (3, (2, 2, 2))])
+def test_elastic_iterates_match_the_oracle(N, E):
+    """Implicit Euler at CFL 2 (sigma = 1/dt, b = u^0/dt) from u^0."""
+    from oracle.ihdg import IHDG
+    s, op, _, mesh = _el(E, N)
+    dt = 4.0 * s.dt_cfl()
+    ih = IHDG(op, 1.0 / dt)
+    u0 = wl.random_fields(9, mesh.nel, (N + 1) ** 3, 5)
+    iterates = [u0]
+    for _ in range(3):
+        iterates.append(ih.iterate(u0 / dt, iterates[-1]))
+    s.ihdg_setup(1.0 / dt)
+    u0d = _dev(u0)
+    for k in (1, 3):
+        u = u0d.clone()
+        its, _ = s.ihdg_solve(u, u_prev=u0d, tol=0.0, max_iter=k)
+        assert its == k
+        assert rel_l2(u.cpu().numpy(), iterates[k]) < 1e-11, k
+
+
+def test_elastic_converged_step_is_the_direct_implicit_step():
+    from oracle.ihdg import IHDG
+    s, op, _, mesh = _el((3, 3, 2), 1)
+    dt = 4.0 * s.dt_cfl()
+    ih = IHDG(op, 1.0 / dt)
+    u0 = wl.random_fields(9, mesh.nel, 8, 6)
+    ud = ih.direct(u0 / dt)
+    _, its_or, _ = ih.solve(u0 / dt, u0, tol=1e-10)
+    s.ihdg_setup(1.0 / dt)
+    u0d = _dev(u0)
+    u = u0d.clone()
+    its, change = s.ihdg_solve(u, u_prev=u0d, tol=1e-10, max_iter=500)
+    assert abs(its - its_or) <= 1 and change < 1e-10
+    assert rel_l2(u.cpu().numpy(), ud) < 1e-9
+
+
+@pytest.mark.parametrize("scheme", ["euler", "crank_nicolson"])
+def test_elastic_implicit_steps_satisfy_the_energy_identities(scheme):
+    """4^3 elements, N = 2, CFL 2, converged to 1e-13 on the GPU:
+    implicit Euler  E(u^0) = E(u^1) + E(u^1 - u^0) - dt <u^1, L u^1>_Q,
+    Crank-Nicolson  E(u^1) - E(u^0) = dt/4 <u^1 + u^0, L(u^1 + u^0)>_Q,
+    with E and the rate from the oracle on the oracle's nodes."""
+    import torch
+    s, op, _, mesh = _el(4, 2)
+    dt = 4.0 * s.dt_cfl()
+    u0 = wl.random_fields(9, mesh.nel, 27, 7)
+    u0d = _dev(u0)
+    sigma = 1.0 / dt if scheme == "euler" else 2.0 / dt
+    f = None
+    if scheme == "crank_nicolson":
+        f = torch.empty_like(u0d)
+        s.rhs(u0d, f)
+    s.ihdg_setup(sigma)
+    u = u0d.clone()
+    its, change = s.ihdg_solve(u, u_prev=u0d, f=f, tol=1e-13, max_iter=2000)
+    assert change < 1e-13, (its, change)
+    u1 = u.cpu().numpy()
+    E0, E1 = op.energy(u0), op.energy(u1)
+    if scheme == "euler":
+        gap = E0 - (E1 + op.energy(u1 - u0) - dt * op.energy_rate(u1))
+    else:
+        gap = (E1 - E0) - 0.25 * dt * op.energy_rate(u1 + u0)
+    assert E1 < E0
+    assert abs(gap) < 1e-10 * E0, (gap, E0)
+
+
+def test_elastic_refusals():
+    from paper_1711_01175_gb300 import Solver, capi, reference_nodes
+    s, _, _, _ = _el((2, 2, 2), 1, oracle_side=False, precision="mixed")
+    assert capi.dgw_ihdg_setup(s._ctx, 10.0, None) == -7              # FP64 only
+    s4, _, _, _ = _el((2, 2, 2), 4, oracle_side=False)
+    assert capi.dgw_ihdg_setup(s4._ctx, 10.0, None) == -7             # N <= 3
+    mesh = wl.structured_hex_mesh((2, 2, 1), (True, True, True))
+    nm = Solver(1)
+    nm.upload_mesh(wl.warped_node_coords(mesh, reference_nodes(1)[0], 0.0), mesh.etoe, mesh.etof, mesh.orient,
+                   mesh.bc)
+    assert capi.dgw_ihdg_setup(nm._ctx, 10.0, None) == -2             # material first
+    nm.upload_material(*wl.homogeneous_material(mesh.nel))
+    assert capi.dgw_ihdg_setup(nm._ctx, 10.0, None) == -7             # one element thick and periodic in z

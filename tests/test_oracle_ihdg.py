@@ -161,3 +161,70 @@ def test_shallow_water_iteration_counts_of_the_paper(E, N):
         counts.append(its)
     assert abs(counts[0] - paper[0]) <= 3 and abs(counts[1] - paper[1]) <= 3, (counts, paper)
     assert counts[0] > counts[1]
+
+
+# ---- the elastic system (velocity-stress, heterogeneous, curvilinear) --------
+#
+# The paper builds iHDG-II on the upwind HDG discretisation of a Friedrichs
+# system; the elastic operator is one (with Q), taken here with the upwind
+# flux.  Pins: the self-only operator is the operator of one element alone; a
+# fixed point solves the implicit step; and the implicit steps obey the exact
+# energy identities of a linear operator L in the Q inner product, with
+# rate(w) = <w, L w>_Q (the oracle's energy_rate, computed independently):
+#   implicit Euler   E(u^0) = E(u^1) + E(u^1 - u^0) - dt rate(u^1),
+#   Crank-Nicolson   E(u^1) - E(u^0) = dt/4 rate(u^1 + u^0).
+# A wrong local block or neighbour term leaves the step unsolved and breaks them.
+
+
+def _el_op(tau=1, E=(3, 3, 2), N=1, seed=3):
+    mesh = wl.structured_hex_mesh(E, (True, True, False), {4: wl.BC_FREE_SURFACE, 5: wl.BC_ABSORBING})
+    r, _ = oracle.gll(N)
+    x = wl.warped_node_coords(mesh, r, 0.05)
+    rho, lam, mu = wl.smooth_random_material(mesh, seed)
+    op = oracle.ElasticDG(N, x, mesh.etoe, mesh.etof, mesh.orient, mesh.bc, rho, lam, mu, tau)
+    dt = oracle.cfl_dt(0.5, oracle.h_min_corner_edges(x, N), op.c_max(), N)
+    return op, x, dt
+
+
+def test_elastic_self_blocks_are_the_operator_of_one_element():
+    from oracle.ihdg import IHDG
+    op, _, dt = _el_op()
+    ih = IHDG(op, 1.0 / dt)
+    for K in (0, 4, 17):            # free-surface bottom, absorbing top
+        for qj in (0, 5, 3 * op.Np + 2, 8 * op.Np + 7):
+            u = np.zeros((9, op.nel, op.Np))
+            u[qj // op.Np, K, qj % op.Np] = 1.0
+            col = op.rhs(u, source=False)[:, K].reshape(-1)
+            assert np.allclose(ih.Lself[K][:, qj], col, atol=1e-12 * np.abs(col).max())
+
+
+def test_elastic_implicit_euler_by_ihdg():
+    """sigma = 1/dt (CFL 2), b = u^0/dt: the converged iterate is the direct
+    implicit step and satisfies the implicit-Euler energy identity."""
+    from oracle.ihdg import IHDG
+    op, x, dt0 = _el_op()
+    dt = 4.0 * dt0
+    ih = IHDG(op, 1.0 / dt)
+    u0 = wl.random_fields(9, op.nel, op.Np, 11)
+    b = u0 / dt
+    u, its, hist = ih.solve(b, u0, tol=1e-13, max_iter=400)
+    assert hist[-1] < 1e-13
+    ud = ih.direct(b)
+    assert ih.norm(u - ud) < 1e-10 * ih.norm(ud)
+    E0, E1, Ed = op.energy(u0), op.energy(u), op.energy(u - u0)
+    rate = op.energy_rate(u)
+    assert rate < 0 and E1 < E0
+    assert abs(E0 - (E1 + Ed - dt * rate)) < 1e-11 * E0
+
+
+def test_elastic_crank_nicolson_by_ihdg_energy_identity():
+    from oracle.ihdg import IHDG
+    op, x, dt0 = _el_op()
+    dt = 4.0 * dt0
+    ih = IHDG(op, 2.0 / dt)
+    u0 = wl.random_fields(9, op.nel, op.Np, 12)
+    b = ih.sigma * u0 + op.rhs(u0, source=False)
+    u, its, hist = ih.solve(b, u0, tol=1e-13, max_iter=400)
+    assert hist[-1] < 1e-13
+    E0, E1 = op.energy(u0), op.energy(u)
+    assert abs((E1 - E0) - 0.25 * dt * op.energy_rate(u + u0)) < 1e-11 * E0
