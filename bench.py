@@ -617,9 +617,57 @@ def run_ihdg(args):
         cn.append({"dt": dt, "iterations": k, "paper_table_iterations": table_sw.get((Es * Es, Ns), (None, None))[
             0 if dt == 0.1 else 1], "solve_ms": (time.perf_counter() - t0) * 1e3})
     sw.close()
+    elastic = run_ihdg_elastic(args) if args.ihdg_elastic_E > 0 else None
     return {"steady": steady, "locally_implicit": {"mesh": f"{Ei}^3", "N": N, "beta": list(b2), "runs": implicit},
             "shallow_water_crank_nicolson": {"mesh": f"{Es}x{Es}", "N": Ns, "first_step": cn},
-            "precision": "fp64"}
+            "elastic_locally_implicit": elastic, "precision": "fp64"}
+
+
+def run_ihdg_elastic(args):
+    """iHDG-II on the elastic system: implicit Euler steps of the large
+    workload's recipe (heterogeneous medium, warped mesh, free surface and
+    absorbing faces, Gaussian stress pulse) at E^3 elements and N = 2, FP64 and
+    upwind, at CFL 1, 2 and 5: set-up time, iterations per step (1e-10
+    criterion), time per step, and the HBM rate of the local solves (the
+    inverses, nel (9 Np)^2 doubles, are read once per iteration)."""
+    import torch
+    from paper_1711_01175_gb300 import Solver, reference_nodes
+    N, E = 2, args.ihdg_elastic_E
+    w = wl.large_config(E=E, N=N).build(reference_nodes(N)[0])
+    mesh = w["mesh"]
+    nb = 9 * (N + 1) ** 3
+    inv_bytes = float(nb) * nb * 8 * mesh.nel
+    runs = []
+    for cfl in (1.0, 2.0, 5.0):
+        s = Solver(N, cfl=cfl)
+        s.upload_mesh(w["x"], mesh.etoe, mesh.etof, mesh.orient, mesh.bc)
+        s.upload_material(w["rho"], w["lam"], w["mu"])
+        dt = s.dt_cfl()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.ihdg_setup(1.0 / dt)
+        setup_s = time.perf_counter() - t0
+        um = torch.from_numpy(w["u0"]).cuda()
+        u = um.clone()
+        s.ihdg_solve(u, u_prev=um, tol=0.0, max_iter=2)          # warm-up
+        u.copy_(um)
+        counts = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.ihdg_steps):
+            k, _ = s.ihdg_solve(u, u_prev=um, tol=1e-10, max_iter=1000)
+            counts.append(k)
+            um.copy_(u)
+        wall = time.perf_counter() - t0
+        its = sum(counts)
+        runs.append({"cfl": cfl, "dt": dt, "setup_s": setup_s, "steps": args.ihdg_steps,
+                     "iterations_per_step": counts, "ms_per_step": wall * 1e3 / args.ihdg_steps,
+                     "ms_per_iteration": wall * 1e3 / its,
+                     "local_solve_hbm_gbs": inv_bytes * its / wall / 1e9})
+        s.close()
+        del u, um
+    return {"mesh": f"{E}^3", "N": N, "workload": "large recipe (seed 1 medium, warp 0.1, Gaussian pulse)",
+            "block_rows": nb, "inverse_bytes": inv_bytes, "runs": runs}
 
 
 def build_workload_oracle(name, E=None):
@@ -651,6 +699,8 @@ def main():
     ap.add_argument("--ihdg-implicit-E", type=int, default=16)
     ap.add_argument("--ihdg-steps", type=int, default=5)
     ap.add_argument("--fr-E", type=int, default=64, help="transport mesh edge (shallow water: 8x this, one layer)")
+    ap.add_argument("--ihdg-elastic-E", type=int, default=16,
+                    help="elastic iHDG-II mesh edge (N = 2; 0 skips the elastic part)")
     ap.add_argument("--fr-steps", type=int, default=20)
     ap.add_argument("--adj-E", type=int, default=16, help="adjoint mesh edge (the full recipe: 32)")
     ap.add_argument("--adj-steps", type=int, default=40, help="(the full recipe: 500)")
