@@ -100,13 +100,14 @@ def step_bytes_per_dof(N, real_bytes):
 
 def algorithmic_flops_per_element(N):
     """Flops of one fused stage per element as the kernel's arithmetic is written:
-    per node and direction, A(m)u (27), two length-(N+1) contractions of 9 fields
-    (36(N+1)), A(m) du (27) and two 9-wide accumulations (18); volume scale (10),
-    Q^{-1} (14) and the LSRK update (45) per node; per face node the flux
-    difference (jump 9, A(m) 27, |A(m)| 42, scaling 27) and its lift (9)."""
+    per node, direction and line node b, the summed metric D_ab (m_a + m_b)
+    (3 adds, 3 multiplies) and A(D_ab (m_a + m_b)) u_b accumulated (18 FMA =
+    36 flops); volume scale (10), Q^{-1} (14) and the LSRK update (45) per node;
+    per face node the flux difference (jump 9, A(m) 27, |A(m)| 42, scaling 27)
+    and its lift (9)."""
     n = N + 1
     Np, nf = n ** 3, n * n
-    per_node = 3 * (27 + 36 * n + 27 + 18) + 10 + 14 + 45
+    per_node = 3 * n * (3 + 3 + 36) + 10 + 14 + 45
     per_face_node = 9 + 27 + 42 + 27 + 9
     return Np * per_node + 6 * nf * per_face_node
 

@@ -8,9 +8,9 @@
 //        acc += D_i (A(Ja^i) u)   [conservative part]
 //        acc += A(Ja^i) (D_i u)   [non-conservative part]
 //      and vol = -1/2 * (1/J) * acc, with A(m)u = -(sigma m, Voigt(sym(m (x) v))).
-//      FP64 stages A(Ja^i)u of the tile in shared memory per direction; FP32
-//      recomputes A(D_ab Ja^i_b) u_b at each contraction node instead (no
-//      staging, no barrier between directions).
+//      A is linear in m, so along the line through node a both parts are
+//      sum_b A(D_ab (Ja^i_a + Ja^i_b)) u_b, accumulated from the state and
+//      metric tiles (no staging, no barrier between directions).
 //   3. Face items (EPB*6*nf of them, spread over all threads): own trace from
 //      smem, neighbour trace from HBM/L2 through the neighbour map (or the
 //      boundary ghost), flux difference 1/2 (A(m) - tau S(m))(u^- - u^+) with
@@ -170,12 +170,8 @@ struct StageSmem {
   using S = Shape<N>;
   static constexpr int PK = Pack<Real>::PK;
   static constexpr size_t u_off = 0;                                    // Real [NTILE][PK] state
-  static constexpr size_t f_off = u_off + sizeof(Real) * S::NTILE * PK;  // Real [NTILE][PK] flux / face fluxes
-  // FP64 stages A(Ja^i)u in this region before the face fluxes reuse it; FP32
-  // recomputes A(Ja^i)u at the contraction nodes and keeps only the face fluxes.
-  static constexpr size_t fwords =
-      (std::is_same<Real, float>::value || S::NTILE * PK < 9 * S::NFACE_ITEMS) ? 9 * S::NFACE_ITEMS : S::NTILE * PK;
-  static constexpr size_t fbytes = sizeof(Real) * fwords;
+  static constexpr size_t f_off = u_off + sizeof(Real) * S::NTILE * PK;  // Real [9][NFACE_ITEMS] face fluxes
+  static constexpr size_t fbytes = sizeof(Real) * 9 * S::NFACE_ITEMS;
   static constexpr size_t g_off = f_off + ((fbytes + 15) / 16) * 16;     // Real [NTILE][PK] Ja, 1/J
   static constexpr size_t d_off = g_off + sizeof(Real) * S::NTILE * PK;  // Real [n*n]
   static constexpr size_t e_off = ((d_off + sizeof(Real) * S::n * S::n + 15) / 16) * 16;  // double [32] reduction
@@ -215,8 +211,7 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
   constexpr int NTILE = S::NTILE, NFI = S::NFACE_ITEMS, PK = L::PK;
 
   Real* u_s = reinterpret_cast<Real*>(smem_raw + L::u_off);
-  Real* f_s = reinterpret_cast<Real*>(smem_raw + L::f_off);
-  Real* x_s = f_s;                       // face fluxes [9][NFI] reuse the flux tile
+  Real* x_s = reinterpret_cast<Real*>(smem_raw + L::f_off);   // face fluxes [9][NFI]
   Real* g_s = reinterpret_cast<Real*>(smem_raw + L::g_off);
   Real* D_s = reinterpret_cast<Real*>(smem_raw + L::d_off);
   double* red_s = reinterpret_cast<double*>(smem_raw + L::e_off);
@@ -235,10 +230,12 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
 
   if (p.pf_elems > 0) {
     // L2 prefetch of the tile that starts about two CTAs per SM later, so that its
-    // loads hit L2.  The tile must end before the last element: the 16-byte
-    // rounding of the range then stays inside every field of the buffers.
+    // loads hit L2: the state, metric terms and register, and the small per-element
+    // arrays read behind them (neighbour map, face impedances, medium).  The tile
+    // must end before the last element: the 16-byte rounding of each range then
+    // stays inside every field of the buffers.
     const long long ep = e0 + p.pf_elems;
-    if (t < 28 && ep + EPB < p.nel) {
+    if (t < 36 && ep + EPB < p.nel) {
       const size_t off = static_cast<size_t>(ep) * Np;
       const size_t len = static_cast<size_t>(EPB) * Np;
       if (t < 9) {
@@ -247,9 +244,23 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
       } else if (t < 19) {
         const Real* a = geo + (t - 9) * fstride + off;
         prefetch_l2(a, a + len);
-      } else if (LSRK && !first) {
-        const double* a = p.res + (t - 19) * fstride + off;
-        prefetch_l2(a, a + len);
+      } else if (t < 28) {
+        if (LSRK && !first) {
+          const double* a = p.res + (t - 19) * fstride + off;
+          prefetch_l2(a, a + len);
+        }
+      } else if (t == 28) {
+        const int* a = p.vmapP + static_cast<size_t>(ep) * 6 * nf;
+        prefetch_l2(a, a + static_cast<size_t>(EPB) * 6 * nf);
+      } else if (t < 33) {
+        if (p.fz != nullptr) {
+          const Real* a = static_cast<const Real*>(p.fz) + static_cast<size_t>(t - 29) * p.nel * 6 + ep * 6;
+          prefetch_l2(a, a + EPB * 6);
+        }
+      } else if (p.mat != nullptr && ep + EPB + 16 / static_cast<long long>(sizeof(Real)) <= p.nel) {
+        // one Real per element: keep 16 bytes of elements after the range
+        const Real* a = static_cast<const Real*>(p.mat) + static_cast<size_t>(t - 33) * p.nel + ep;
+        prefetch_l2(a, a + EPB);
       }
     }
   }
@@ -286,84 +297,52 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
 #pragma unroll
   for (int q = 0; q < 9; ++q) acc[q] = 0;
 
-  if constexpr (std::is_same<Real, float>::value) {
-    // FP32: A_+(Ja^i) u at each contraction node is recomputed from the state
-    // and metric tiles (no staging, no barrier between directions).
-    if (in_tile) {
-#pragma unroll
-      for (int dir = 0; dir < 3; ++dir) {
-        const int stride = dir == 0 ? 1 : (dir == 1 ? n : nf);
-        const int a = dir == 0 ? ix : (dir == 1 ? iy : iz);
-        const int base = t - a * stride;
-        Real ds[9];
-#pragma unroll
-        for (int q = 0; q < 9; ++q) ds[q] = 0;
-#pragma unroll
-        for (int b = 0; b < n; ++b) {
-          const Real Dab = D_s[a * n + b];
-          const int nb = base + b * stride;
-          Real w[10];
-          V::load9(u_s + nb * PK, w);
-          const float4 mb = reinterpret_cast<const float4*>(g_s + nb * PK)[dir];
-          // D_ab A_+(m_b) u_b = A_+(D_ab m_b) u_b, accumulated term by term
-          acc_Apos(Dab * mb.x, Dab * mb.y, Dab * mb.z, w, acc);
-#pragma unroll
-          for (int q = 0; q < 9; ++q) ds[q] += Dab * w[q];
-        }
-        const float4 mt = reinterpret_cast<const float4*>(g_s + t * PK)[dir];
-        Real G[9];
-        apply_Apos(mt.x, mt.y, mt.z, ds, G);
-#pragma unroll
-        for (int q = 0; q < 9; ++q) acc[q] += G[q];
-      }
-    }
-  } else {
+  // Volume term, direction by direction along the line of n nodes through this
+  // one (a its index on the line): the conservative part D_i(A_+(Ja^i) u) and
+  // the non-conservative part A_+(Ja^i)(D_i u) together are
+  //   sum_b D_ab A_+(m_b) u_b + A_+(m_a) sum_b D_ab u_b = sum_b A_+(D_ab (m_a + m_b)) u_b,
+  // m = Ja^i (A_+ is linear in m), accumulated term by term from the state and
+  // metric tiles (no staging, no barrier between directions).
+  if (in_tile) {
 #pragma unroll
     for (int dir = 0; dir < 3; ++dir) {
-      Real m1 = 0, m2 = 0, m3 = 0;
-      if (in_tile) {
-        m1 = g_s[t * PK + 3 * dir + 0];
-        m2 = g_s[t * PK + 3 * dir + 1];
-        m3 = g_s[t * PK + 3 * dir + 2];
-        Real w[10], F[10];
-        V::load9(u_s + t * PK, w);
-        apply_Apos(m1, m2, m3, w, F);
-        F[9] = 0;
-        V::store10(f_s + t * PK, F);
+      const int stride = dir == 0 ? 1 : (dir == 1 ? n : nf);
+      const int a = dir == 0 ? ix : (dir == 1 ? iy : iz);
+      const int base = t - a * stride;
+      Real ma0, ma1, ma2;
+      if constexpr (std::is_same<Real, float>::value) {
+        const float4 mt = reinterpret_cast<const float4*>(g_s + t * PK)[dir];
+        ma0 = mt.x;
+        ma1 = mt.y;
+        ma2 = mt.z;
+      } else {
+        ma0 = g_s[t * PK + gslot<Real>(dir, 0)];
+        ma1 = g_s[t * PK + gslot<Real>(dir, 1)];
+        ma2 = g_s[t * PK + gslot<Real>(dir, 2)];
       }
-      __syncthreads();
-      if (in_tile) {
-        const int stride = dir == 0 ? 1 : (dir == 1 ? n : nf);
-        const int a = dir == 0 ? ix : (dir == 1 ? iy : iz);
-        const int base = t - a * stride;
-        Real Drow[n];
-  #pragma unroll
-        for (int b = 0; b < n; ++b) Drow[b] = D_s[a * n + b];
-        // D_i (A_+(Ja^i) u) and A_+(Ja^i)(D_i u), both accumulated into acc
-        Real ds[9];
-  #pragma unroll
-        for (int q = 0; q < 9; ++q) ds[q] = 0;
-  #pragma unroll
-        for (int b = 0; b < n; ++b) {
-          Real F[10];
-          V::load9(f_s + (base + b * stride) * PK, F);
-  #pragma unroll
-          for (int q = 0; q < 9; ++q) acc[q] += Drow[b] * F[q];
+#pragma unroll
+      for (int b = 0; b < n; ++b) {
+        const Real Dab = D_s[a * n + b];
+        const int nb = base + b * stride;
+        Real w[10];
+        V::load9(u_s + nb * PK, w);
+        Real mb0, mb1, mb2;
+        if constexpr (std::is_same<Real, float>::value) {
+          const float4 mb = reinterpret_cast<const float4*>(g_s + nb * PK)[dir];
+          mb0 = mb.x;
+          mb1 = mb.y;
+          mb2 = mb.z;
+        } else {
+          mb0 = g_s[nb * PK + gslot<Real>(dir, 0)];
+          mb1 = g_s[nb * PK + gslot<Real>(dir, 1)];
+          mb2 = g_s[nb * PK + gslot<Real>(dir, 2)];
         }
-  #pragma unroll
-        for (int b = 0; b < n; ++b) {
-          Real w[10];
-          V::load9(u_s + (base + b * stride) * PK, w);
-  #pragma unroll
-          for (int q = 0; q < 9; ++q) ds[q] += Drow[b] * w[q];
-        }
-        acc_Apos(m1, m2, m3, ds, acc);
+        acc_Apos(Dab * (ma0 + mb0), Dab * (ma1 + mb1), Dab * (ma2 + mb2), w, acc);
       }
-      __syncthreads();
     }
   }
 
-  // Face items: lifted flux differences (x_s now aliases the free flux tile).
+  // Face items: lifted flux differences.
   {
     const Real* fz = static_cast<const Real*>(p.fz);
     const Real tau = pick<Real>(p.tau, p.tau_f);
