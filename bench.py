@@ -99,15 +99,18 @@ def step_bytes_per_dof(N, real_bytes):
 
 
 def algorithmic_flops_per_element(N):
-    """Flops of one fused stage per element as the kernel's arithmetic is written:
-    per node, direction and line node b, the summed metric D_ab (m_a + m_b)
-    (3 adds, 3 multiplies) and A(D_ab (m_a + m_b)) u_b accumulated (18 FMA =
-    36 flops); volume scale (10), Q^{-1} (14) and the LSRK update (45) per node;
-    per face node the flux difference (jump 9, A(m) 27, |A(m)| 42, scaling 27)
-    and its lift (9)."""
+    """FP64 flops of one fused stage per element as the kernel's arithmetic is
+    written.  Volume term per node and direction: N <= 5, for each line node b
+    the summed metric D_ab (m_a + m_b) (3 adds, 3 multiplies) and
+    A(D_ab (m_a + m_b)) u_b accumulated (18 FMA = 36 flops); N >= 6 (the staged
+    form), A(m)u (27), two length-(N+1) contractions of 9 fields (36(N+1)),
+    A(m) du (27) and two 9-wide accumulations (18).  Volume scale (10), Q^{-1}
+    (14) and the LSRK update (45) per node; per face node the flux difference
+    (jump 9, A(m) 27, |A(m)| 42, scaling 27) and its lift (9)."""
     n = N + 1
     Np, nf = n ** 3, n * n
-    per_node = 3 * n * (3 + 3 + 36) + 10 + 14 + 45
+    volume = 3 * (27 + 36 * n + 27 + 18) if N >= 6 else 3 * n * (3 + 3 + 36)
+    per_node = volume + 10 + 14 + 45
     per_face_node = 9 + 27 + 42 + 27 + 9
     return Np * per_node + 6 * nf * per_face_node
 
@@ -707,7 +710,7 @@ def main():
     ap.add_argument("--adj-steps", type=int, default=40, help="(the full recipe: 500)")
     ap.add_argument("--adj-receivers", type=int, default=8, help="(the full recipe: 32)")
     ap.add_argument("--adj-checkpoint", type=int, default=10, help="(the full recipe: 50)")
-    ap.add_argument("--serve-requests", type=int, default=48,
+    ap.add_argument("--serve-requests", type=int, default=160,
                     help="requests of the served-latency run (the full recipe: 2000)")
     ap.add_argument("--serve-rate", type=float, default=80.0, help="Poisson arrival rate per second")
     ap.add_argument("--serve-max-E", type=int, default=20, help="largest mesh edge (the full recipe: 48)")

@@ -165,13 +165,29 @@ __device__ __forceinline__ void prefetch_l2(const void* lo, const void* hi) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(a), "r"((unsigned)(b - a)) : "memory");
 }
 
+// Volume-term form.  Combined: per direction and line node b, A_+(D_ab (m_a + m_b)) u_b
+// (24 operations).  Staged: A_+(m) u of the tile staged in shared memory, then
+// the two contractions and A_+(m_a) applied to D u (36 + 18 n operations per
+// node and direction, two barriers per direction).  FP64 is bound by its FP64
+// pipe and takes the staged form where it has fewer operations (n >= 7); FP32
+// always takes the combined form (fewer instructions, no barriers).
+template <int N, typename Real>
+__host__ __device__ constexpr bool staged_volume() {
+  return std::is_same<Real, double>::value && N >= 6;
+}
+
 template <int N, typename Real>
 struct StageSmem {
   using S = Shape<N>;
   static constexpr int PK = Pack<Real>::PK;
   static constexpr size_t u_off = 0;                                    // Real [NTILE][PK] state
-  static constexpr size_t f_off = u_off + sizeof(Real) * S::NTILE * PK;  // Real [9][NFACE_ITEMS] face fluxes
-  static constexpr size_t fbytes = sizeof(Real) * 9 * S::NFACE_ITEMS;
+  // Real [9][NFACE_ITEMS] face fluxes; the staged volume form first keeps
+  // A_+(Ja^i)u [NTILE][PK] of one direction in the same region.
+  static constexpr size_t f_off = u_off + sizeof(Real) * S::NTILE * PK;
+  static constexpr size_t fwords = (staged_volume<N, Real>() && S::NTILE * PK > 9 * S::NFACE_ITEMS)
+                                       ? S::NTILE * PK
+                                       : 9 * S::NFACE_ITEMS;
+  static constexpr size_t fbytes = sizeof(Real) * fwords;
   static constexpr size_t g_off = f_off + ((fbytes + 15) / 16) * 16;     // Real [NTILE][PK] Ja, 1/J
   static constexpr size_t d_off = g_off + sizeof(Real) * S::NTILE * PK;  // Real [n*n]
   static constexpr size_t e_off = ((d_off + sizeof(Real) * S::n * S::n + 15) / 16) * 16;  // double [32] reduction
@@ -211,7 +227,8 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
   constexpr int NTILE = S::NTILE, NFI = S::NFACE_ITEMS, PK = L::PK;
 
   Real* u_s = reinterpret_cast<Real*>(smem_raw + L::u_off);
-  Real* x_s = reinterpret_cast<Real*>(smem_raw + L::f_off);   // face fluxes [9][NFI]
+  Real* f_s = reinterpret_cast<Real*>(smem_raw + L::f_off);   // staged A_+(Ja^i)u (staged form)
+  Real* x_s = f_s;                                             // then the face fluxes [9][NFI]
   Real* g_s = reinterpret_cast<Real*>(smem_raw + L::g_off);
   Real* D_s = reinterpret_cast<Real*>(smem_raw + L::d_off);
   double* red_s = reinterpret_cast<double*>(smem_raw + L::e_off);
@@ -301,9 +318,49 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
   // one (a its index on the line): the conservative part D_i(A_+(Ja^i) u) and
   // the non-conservative part A_+(Ja^i)(D_i u) together are
   //   sum_b D_ab A_+(m_b) u_b + A_+(m_a) sum_b D_ab u_b = sum_b A_+(D_ab (m_a + m_b)) u_b,
-  // m = Ja^i (A_+ is linear in m), accumulated term by term from the state and
-  // metric tiles (no staging, no barrier between directions).
-  if (in_tile) {
+  // m = Ja^i (A_+ is linear in m).  Combined form: the right-hand side,
+  // accumulated term by term from the state and metric tiles (no staging, no
+  // barrier between directions).  Staged form: the left-hand side, with
+  // A_+(m_b) u_b staged per direction.
+  if constexpr (staged_volume<N, Real>()) {
+#pragma unroll
+    for (int dir = 0; dir < 3; ++dir) {
+      Real m1 = 0, m2 = 0, m3 = 0;
+      if (in_tile) {
+        m1 = g_s[t * PK + gslot<Real>(dir, 0)];
+        m2 = g_s[t * PK + gslot<Real>(dir, 1)];
+        m3 = g_s[t * PK + gslot<Real>(dir, 2)];
+        Real w[10], F[10];
+        V::load9(u_s + t * PK, w);
+        apply_Apos(m1, m2, m3, w, F);
+        F[9] = 0;
+        V::store10(f_s + t * PK, F);
+      }
+      __syncthreads();
+      if (in_tile) {
+        const int stride = dir == 0 ? 1 : (dir == 1 ? n : nf);
+        const int a = dir == 0 ? ix : (dir == 1 ? iy : iz);
+        const int base = t - a * stride;
+        Real ds[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) ds[q] = 0;
+#pragma unroll
+        for (int b = 0; b < n; ++b) {
+          const Real Dab = D_s[a * n + b];
+          Real F[10], w[10];
+          V::load9(f_s + (base + b * stride) * PK, F);
+          V::load9(u_s + (base + b * stride) * PK, w);
+#pragma unroll
+          for (int q = 0; q < 9; ++q) {
+            acc[q] += Dab * F[q];
+            ds[q] += Dab * w[q];
+          }
+        }
+        acc_Apos(m1, m2, m3, ds, acc);
+      }
+      __syncthreads();
+    }
+  } else if (in_tile) {
 #pragma unroll
     for (int dir = 0; dir < 3; ++dir) {
       const int stride = dir == 0 ? 1 : (dir == 1 ? n : nf);
