@@ -82,7 +82,7 @@ typedef struct {
 } dgw_config;
 
 /* ABI version of this header (bumped on any signature change). */
-#define DGW_ABI_VERSION 7
+#define DGW_ABI_VERSION 8
 int dgw_abi_version(void);
 
 /* GLL nodes r[0..N] (ascending, r[0] = -1, r[N] = +1) and weights w[0..N]
@@ -154,12 +154,25 @@ dgw_status dgw_stage(dgw_ctx* ctx, const double* u_in, double* u_out, double* re
 dgw_status dgw_stage_energy(dgw_ctx* ctx, const double* u_in, double* u_out, double* res, int stage,
                             double t, double dt, double* energy_out, void* stream);
 
-/* nsteps LSRK(5,4) steps of size dt from time t0, in place on u and res
- * (res must hold zeros, or the register of the previous step -- its value is
- * multiplied by a_0 = 0).  Uses a context-owned second state buffer for the
- * stage ping-pong and copies the final state back into u. */
+/* nsteps LSRK(5,4) steps of size dt from time t0, in place on u and res.
+ * The first stage does not read the register (a_0 = 0), so the incoming
+ * contents of res never matter; on return res holds the register of the last
+ * stage.  res may be NULL: the context keeps the register in its own device
+ * buffer.  Uses a context-owned second state buffer for the stage ping-pong
+ * and copies the final state back into u.  Host buffers (u or res not device
+ * memory) are staged through context buffers: u is copied in and out, res
+ * only out (and not at all for nsteps = 0); the call then synchronises
+ * `stream`. */
 dgw_status dgw_step(dgw_ctx* ctx, double* u, double* res, double t0, double dt, int nsteps,
                     void* stream);
+
+/* dgw_step whose last stage also accumulates the discrete energy of the new
+ * state (as dgw_stage_energy), so advancing a state and reading its energy
+ * costs no second pass over it; with host buffers, no second upload.
+ * nsteps >= 1; energy_out: host double; synchronises `stream`.
+ * DGW_ERR_UNSTABLE if the energy is not finite. */
+dgw_status dgw_step_energy(dgw_ctx* ctx, double* u, double* res, double t0, double dt, int nsteps,
+                           double* energy_out, void* stream);
 
 /* Discrete energy E = 1/2 sum_K sum_nodes w J u^T Q u, accumulated in FP64
  * with a fixed reduction order (bit-reproducible for a given mesh).

@@ -45,6 +45,7 @@ SIGNATURES = {
     "dgw_stage": (_I, [_P, _P, _P, _P, _I, _D, _D, _P]),
     "dgw_stage_energy": (_I, [_P, _P, _P, _P, _I, _D, _D, ctypes.POINTER(_D), _P]),
     "dgw_step": (_I, [_P, _P, _P, _D, _D, _I, _P]),
+    "dgw_step_energy": (_I, [_P, _P, _P, _D, _D, _I, ctypes.POINTER(_D), _P]),
     "dgw_energy": (_I, [_P, _P, ctypes.POINTER(_D), _P]),
     "dgw_source_set": (_I, [_P, _I64, _P, _P, _D, _D]),
     "dgw_receivers_set": (_I, [_P, _I, _P, _P]),
@@ -139,6 +140,12 @@ def dgw_stage_energy(ctx, u_in, u_out, res, stage, t, dt, stream):
 
 def dgw_step(ctx, u, res, t0, dt, nsteps, stream):
     return load().dgw_step(ctx, u, res, t0, dt, nsteps, stream)
+
+
+def dgw_step_energy(ctx, u, res, t0, dt, nsteps, stream):
+    out = _D()
+    st = load().dgw_step_energy(ctx, u, res, t0, dt, nsteps, ctypes.byref(out), stream)
+    return st, out.value
 
 
 def dgw_energy(ctx, u, stream):

@@ -585,31 +585,43 @@ dgw_status dgw_stage_energy(dgw_ctx* c, const double* u_in, double* u_out, doubl
   return DGW_OK;
 }
 
-dgw_status dgw_step(dgw_ctx* c, double* u, double* res, double t0, double dt, int nsteps, void* stream) {
+}  // extern "C"
+
+namespace {
+
+// nsteps LSRK(5,4) steps of u (res: the register, or NULL for the context's
+// own); with energy_out, the last stage also accumulates the energy of the
+// new state.  The first stage never reads the register (a_0 = 0), so host
+// buffers copy only u in.
+dgw_status step_impl(dgw_ctx* c, double* u, double* res, double t0, double dt, int nsteps, double* energy_out,
+                     void* stream) {
   dgw_status st = ready(c);
   if (st != DGW_OK) return st;
-  if (!u || !res || u == res) return fail(c, DGW_ERR_ARG, "u and res must be distinct non-null buffers");
+  if (!u || u == res) return fail(c, DGW_ERR_ARG, "u must be non-null and distinct from res");
   if (nsteps < 0) return fail(c, DGW_ERR_ARG, "nsteps must be >= 0");
+  if (energy_out && nsteps < 1) return fail(c, DGW_ERR_ARG, "the fused energy needs nsteps >= 1");
   if (!std::isfinite(dt)) return fail(c, DGW_ERR_ARG, "dt must be finite");
   if (set_device(c) != DGW_OK) return DGW_ERR_CUDA;
   cudaStream_t s = (cudaStream_t)stream;
   const size_t bytes = (size_t)c->nel * Np_of(c->cfg.N) * c->m * sizeof(double);
-  const bool host = !is_device_ptr(u) || !is_device_ptr(res);
+  const bool host = !is_device_ptr(u) || (res && !is_device_ptr(res));
   double* ud = u;
   double* rd = res;
-  if (host) {
+  if (host || !res) {
     if ((st = ensure_staging(c, true)) != DGW_OK) return st;
-    ud = c->stage_u;
     rd = c->stage_res;
+  }
+  if (host) {
+    ud = c->stage_u;
     DGW_CUDA(c, cudaMemcpyAsync(ud, u, bytes, cudaMemcpyDefault, s), "copy u in");
-    DGW_CUDA(c, cudaMemcpyAsync(rd, res, bytes, cudaMemcpyDefault, s), "copy res in");
   }
   double* cur = ud;
   double* nxt = c->u2;
   for (int k = 0; k < nsteps; ++k) {
     const double tk = t0 + k * dt;
     for (int sidx = 0; sidx < 5; ++sidx) {
-      if ((st = launch_stage(c, cur, nxt, rd, true, kLsrkA[sidx], kLsrkB[sidx], dt, s, nullptr,
+      double* partials = (energy_out && k == nsteps - 1 && sidx == 4) ? c->stage_partials : nullptr;
+      if ((st = launch_stage(c, cur, nxt, rd, true, kLsrkA[sidx], kLsrkB[sidx], dt, s, partials,
                              tk + kLsrkC[sidx] * dt)) != DGW_OK)
         return st;
       double* tmp = cur;
@@ -620,10 +632,34 @@ dgw_status dgw_step(dgw_ctx* c, double* u, double* res, double t0, double dt, in
   if (cur != ud) DGW_CUDA(c, cudaMemcpyAsync(ud, cur, bytes, cudaMemcpyDeviceToDevice, s), "copy state back");
   if (host) {
     DGW_CUDA(c, cudaMemcpyAsync(u, ud, bytes, cudaMemcpyDefault, s), "copy u out");
-    DGW_CUDA(c, cudaMemcpyAsync(res, rd, bytes, cudaMemcpyDefault, s), "copy res out");
+    if (res && nsteps > 0) DGW_CUDA(c, cudaMemcpyAsync(res, rd, bytes, cudaMemcpyDefault, s), "copy res out");
+  }
+  if (energy_out) {
+    double* result = c->stage_partials + c->stage_ctas;
+    DGW_CUDA(c, dgw::launch_energy_final(c->stage_partials, c->stage_ctas, result + 1, result, s), "energy reduction");
+    double value = 0.0;
+    DGW_CUDA(c, cudaMemcpyAsync(&value, result, sizeof(double), cudaMemcpyDeviceToHost, s), "copy energy");
+    DGW_CUDA(c, cudaStreamSynchronize(s), "step energy");
+    *energy_out = value;
+    if (!std::isfinite(value)) return fail(c, DGW_ERR_UNSTABLE, "energy is not finite");
+  } else if (host) {
     DGW_CUDA(c, cudaStreamSynchronize(s), "step");
   }
   return DGW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dgw_status dgw_step(dgw_ctx* c, double* u, double* res, double t0, double dt, int nsteps, void* stream) {
+  return step_impl(c, u, res, t0, dt, nsteps, nullptr, stream);
+}
+
+dgw_status dgw_step_energy(dgw_ctx* c, double* u, double* res, double t0, double dt, int nsteps,
+                           double* energy_out, void* stream) {
+  if (!energy_out) return fail(c, DGW_ERR_ARG, "null energy_out");
+  return step_impl(c, u, res, t0, dt, nsteps, energy_out, stream);
 }
 
 dgw_status dgw_energy(dgw_ctx* c, const double* u, double* energy_out, void* stream) {

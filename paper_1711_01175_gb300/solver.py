@@ -142,10 +142,23 @@ class Solver:
         return val
 
     def step(self, u, res, dt: float, nsteps: int = 1, t0: float = 0.0, stream=None):
+        """nsteps LSRK(5,4) steps in place on u; res receives the last stage's
+        register (None: the context keeps it)."""
         self._field_check(u, "u")
-        self._field_check(res, "res")
-        self._check(capi.dgw_step(self._ctx, _ptr(u), _ptr(res), float(t0), float(dt), int(nsteps),
-                                  _stream_handle(stream)))
+        if res is not None:
+            self._field_check(res, "res")
+        self._check(capi.dgw_step(self._ctx, _ptr(u), None if res is None else _ptr(res), float(t0), float(dt),
+                                  int(nsteps), _stream_handle(stream)))
+
+    def step_energy(self, u, res, dt: float, nsteps: int = 1, t0: float = 0.0, stream=None) -> float:
+        """step, with the energy of the new state accumulated in its last stage."""
+        self._field_check(u, "u")
+        if res is not None:
+            self._field_check(res, "res")
+        st, val = capi.dgw_step_energy(self._ctx, _ptr(u), None if res is None else _ptr(res), float(t0),
+                                       float(dt), int(nsteps), _stream_handle(stream))
+        self._check(st)
+        return val
 
     def energy(self, u, stream=None) -> float:
         self._field_check(u, "u")

@@ -102,5 +102,6 @@ def test_calls_on_null_context_fail_cleanly(lib):
     from paper_1711_01175_gb300 import capi
     assert capi.dgw_rhs(None, None, None, 0.0, None) == -1
     assert capi.dgw_step(None, None, None, 0.0, 0.1, 1, None) == -1
+    assert capi.dgw_step_energy(None, None, None, 0.0, 0.1, 1, None)[0] == -1
     assert capi.dgw_mesh_upload(None, 1, None, None, None, None, None) == -1
     assert capi.dgw_destroy(None) == 0
