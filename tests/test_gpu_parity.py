@@ -305,3 +305,32 @@ def test_call_order_and_argument_errors():
     from paper_1711_01175_gb300 import capi
     assert capi.dgw_adjoint_step(s._ctx, None, None, None, None, 0.0, 0.1, 1, None) == -1
     s.close()
+
+
+def test_size_limits_and_empty_calls():
+    """nel <= 0 and nel Np >= 2^31 (32-bit node indices) are refused before any
+    array is read; nsteps = 0 leaves the state and register as they are; a
+    non-finite dt is refused."""
+    import ctypes
+    import torch
+    from paper_1711_01175_gb300 import Solver, capi, reference_nodes
+    s = Solver(3)
+    one = np.zeros(64, dtype=np.float64)
+    i64 = np.zeros(6, dtype=np.int64)
+    i8 = np.zeros(6, dtype=np.int8)
+    ptrs = [one.ctypes.data, i64.ctypes.data, i8.ctypes.data, i8.ctypes.data, i8.ctypes.data]
+    assert capi.dgw_mesh_upload(s._ctx, 0, *ptrs) == -1
+    assert capi.dgw_mesh_upload(s._ctx, -4, *ptrs) == -1
+    assert capi.dgw_mesh_upload(s._ctx, (1 << 31) // 64 + 1, *ptrs) == -1
+    assert "2^31" in capi.dgw_last_error(s._ctx)
+    mesh = wl.structured_hex_mesh(2)
+    x = wl.warped_node_coords(mesh, reference_nodes(3)[0], 0.05)
+    s.upload_mesh(x, mesh.etoe, mesh.etof, mesh.orient, mesh.bc)
+    s.upload_material(*wl.homogeneous_material(mesh.nel))
+    u0 = wl.random_fields(9, mesh.nel, 64, 3)
+    u = torch.from_numpy(u0).cuda()
+    r = torch.full_like(u, 7.0)
+    s.step(u, r, 1e-3, 0)
+    assert np.array_equal(u.cpu().numpy(), u0) and bool(torch.all(r == 7.0))
+    assert capi.dgw_step(s._ctx, u.data_ptr(), r.data_ptr(), 0.0, float("nan"), 1, None) == -1
+    s.close()
