@@ -105,7 +105,9 @@ dgw_status launch_stage(dgw_ctx* c, const double* u_in, double* out, double* res
   {
     int epb = 0, nthreads = 0;
     dgw::stage_shape(c->cfg.N, &epb, &nthreads);
-    p.pf_elems = 2LL * c->sm_count * epb;
+    // L2 prefetch distance: one CTA per SM ahead (the fastest of 0.5, 1, 1.5, 2,
+    // 4, 8 and 16 CTAs per SM on 64^3, N = 4; longer distances lose L2 reuse)
+    p.pf_elems = 1LL * c->sm_count * epb;
   }
   p.src_elem = c->src_elem;
   p.src_w = c->src_w;

@@ -373,7 +373,7 @@ cudaError_t launch_elastic_operator(const dgw_ctx* c, const double* u, double* o
   StageParams p{};
   int epb = 0, nthreads = 0;
   stage_shape(c->cfg.N, &epb, &nthreads);
-  p.pf_elems = 2LL * c->sm_count * epb;
+  p.pf_elems = 1LL * c->sm_count * epb;
   p.src_elem = -1;
   p.u_in = u;
   p.out = out;

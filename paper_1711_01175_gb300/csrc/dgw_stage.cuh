@@ -246,7 +246,7 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
   const bool first = p.first != 0;
 
   if (p.pf_elems > 0) {
-    // L2 prefetch of the tile that starts about two CTAs per SM later, so that its
+    // L2 prefetch of the tile that starts p.pf_elems elements later, so that its
     // loads hit L2: the state, metric terms and register, and the small per-element
     // arrays read behind them (neighbour map, face impedances, medium).  The tile
     // must end before the last element: the 16-byte rounding of each range then
