@@ -716,7 +716,7 @@ __device__ __forceinline__ double ricker_dev(double t, double f0, double t0) {
 // t + (step + c_s) dt with t read from device memory, so the launches can be
 // replayed from a CUDA graph; CTAs past the tile total exit.
 template <int N, typename Real>
-__global__ void __launch_bounds__(Shape<N>::NT) stage_batch_kernel(const BatchLaunch L, const BatchSet S) {
+__device__ __forceinline__ void stage_batch_body(const BatchLaunch& L, const BatchSet& S) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const long long tile = blockIdx.x;
   if (tile >= S.total_tiles) return;
@@ -761,9 +761,32 @@ __global__ void __launch_bounds__(Shape<N>::NT) stage_batch_kernel(const BatchLa
 }
 
 template <int N, typename Real>
+__global__ void __launch_bounds__(Shape<N>::NT) stage_batch_kernel(const BatchLaunch L, const BatchSet S) {
+  stage_batch_body<N, Real>(L, S);
+}
+
+// FP32 at N = 5 (224 threads): the batched kernel took 64 registers a thread
+// (four CTAs per SM) where the single-solve kernel takes 56 (five); asking for
+// five CTAs restores 56.  Other degrees keep the default allocation.
+template <typename Real>
+__global__ void __launch_bounds__(Shape<5>::NT, 5) stage_batch_kernel_n5(const BatchLaunch L, const BatchSet S) {
+  stage_batch_body<5, Real>(L, S);
+}
+
+template <int N, typename Real>
+constexpr void (*stage_batch_kernel_ptr())(const BatchLaunch, const BatchSet) {
+  if constexpr (N == 5 && std::is_same<Real, float>::value) {
+    return &stage_batch_kernel_n5<float>;
+  } else {
+    return &stage_batch_kernel<N, Real>;
+  }
+}
+
+template <int N, typename Real>
 cudaError_t launch_stage_batch_t(const BatchLaunch& L, const BatchSet& S, int grid, cudaStream_t s) {
   const size_t smem = StageSmem<N, Real>::bytes;
-  stage_batch_kernel<N, Real><<<grid, Shape<N>::NT, smem, s>>>(L, S);
+  constexpr auto kernel = stage_batch_kernel_ptr<N, Real>();
+  kernel<<<grid, Shape<N>::NT, smem, s>>>(L, S);
   return cudaGetLastError();
 }
 
@@ -771,10 +794,10 @@ cudaError_t launch_stage_batch_t(const BatchLaunch& L, const BatchSet& S, int gr
 template <int N, typename Real>
 cudaError_t prepare_stage_batch_t() {
   const size_t smem = StageSmem<N, Real>::bytes;
-  cudaError_t err = cudaFuncSetAttribute(stage_batch_kernel<N, Real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+  constexpr auto kernel = stage_batch_kernel_ptr<N, Real>();
+  cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  return cudaFuncSetAttribute(stage_batch_kernel<N, Real>, cudaFuncAttributePreferredSharedMemoryCarveout,
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                               (int)cudaSharedmemCarveoutMaxShared);
 }
 
