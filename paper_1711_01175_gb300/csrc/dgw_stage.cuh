@@ -425,7 +425,21 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
       Real um[10], du[9];
       V::load9(u_s + sidx * PK, um);
       const int g = p.vmapP[static_cast<size_t>(ei) * 6 * nf + r];
-      if (g >= 0) {
+      // FP32 tiles of several elements (N <= 3): a neighbour node inside this
+      // tile is read from the shared state tile (the same narrowed values) instead
+      // of L2 (mixed N = 2: +5 %; the FP64 path, bound by its FP64 pipe, lost 2-3 %
+      // to the extra branch and keeps the L2 read).
+      long long gl = -1;
+      if constexpr (EPB > 1 && std::is_same<Real, float>::value) {
+        gl = static_cast<long long>(g) - e0 * Np;
+        if (g < 0 || gl >= NTILE) gl = -1;
+      }
+      if (gl >= 0) {
+        Real up[10];
+        V::load9(u_s + gl * PK, up);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) du[q] = um[q] - up[q];
+      } else if (g >= 0) {
 #pragma unroll
         for (int q = 0; q < 9; ++q) du[q] = um[q] - to_real<Real>(p.u_in[q * fstride + g]);
       } else if (g == kGhostFreeSurface) {
