@@ -262,6 +262,39 @@ def test_full_size_large_workload_sampled():
     assert rel_l2(res.cpu().numpy()[:, sample], r1) < FP64_TOL
 
 
+def test_full_size_precision_workload_sampled():
+    """48^3, N=7 (the precision recipe at full size, 110,592 elements, the launch
+    path the bench times): the right-hand side of a random state on sampled
+    elements (interior, free-surface and absorbing layers) computed one by one by
+    the oracle -- FP64 to 1e-12, and the mixed path on the same sample to its
+    FP32 bound."""
+    import torch
+    from paper_1711_01175_gb300 import Solver
+    cfg = wl.precision_config()
+    c = Case(cfg.E, cfg.N, cfg.amplitude, cfg.periodic, cfg.boundary, cfg.order, material=cfg.material_seed)
+    nel, Np = c.mesh.nel, (cfg.N + 1) ** 3
+    rng = np.random.default_rng(4)
+    bottom = np.nonzero(c.mesh.bc[:, 4] == wl.BC_ABSORBING)[0]
+    top = np.nonzero(c.mesh.bc[:, 5] == wl.BC_FREE_SURFACE)[0]
+    sample = np.unique(np.concatenate([rng.choice(nel, 24, replace=False), rng.choice(bottom, 6),
+                                       rng.choice(top, 6), [0, nel - 1]]))
+    u = wl.random_state(nel, Np, 22)
+    want = c.op.rhs(u, sample)
+    err64 = rel_l2(c.gpu_rhs(u)[:, sample], want)
+    print(f"48^3 N=7 sampled: FP64 rel L2 {err64:.3e}")
+    assert err64 < FP64_TOL, err64
+    m = Solver(cfg.N, precision="mixed")
+    m.upload_mesh(c.x_lib, c.mesh.etoe, c.mesh.etof, c.mesh.orient, c.mesh.bc)
+    m.upload_material(c.rho, c.lam, c.mu)
+    ud = torch.from_numpy(u).cuda()
+    out = torch.empty_like(ud)
+    m.rhs(ud, out)
+    err = rel_l2(out.cpu().numpy()[:, sample], want)
+    print(f"48^3 N=7 sampled: mixed rel L2 {err:.3e}")
+    assert err < MIXED_RHS_TOL, err
+    m.close()
+
+
 # -------------------------------------------------------------- argument errors
 def test_call_order_and_argument_errors():
     import torch
