@@ -779,18 +779,21 @@ __global__ void __launch_bounds__(Shape<N>::NT) stage_batch_kernel(const BatchLa
   stage_batch_body<N, Real>(L, S);
 }
 
-// FP32 at N = 5 (224 threads): the batched kernel took 64 registers a thread
-// (four CTAs per SM) where the single-solve kernel takes 56 (five); asking for
-// five CTAs restores 56.  Other degrees keep the default allocation.
-template <typename Real>
-__global__ void __launch_bounds__(Shape<5>::NT, 5) stage_batch_kernel_n5(const BatchLaunch L, const BatchSet S) {
-  stage_batch_body<5, Real>(L, S);
+// FP32 batched kernels with a resident-CTA bound where the default allocation
+// costs a CTA per SM against the single-solve kernel: N = 3 (256 threads) took
+// 62 registers (four CTAs) against 48 (five), N = 5 (224 threads) 64 (four)
+// against 56 (five).  Asking for five CTAs gives 48 and 56 registers without
+// spills.  Other degrees keep the default allocation.
+template <int N, typename Real, int MIN_CTAS>
+__global__ void __launch_bounds__(Shape<N>::NT, MIN_CTAS)
+    stage_batch_kernel_bounded(const BatchLaunch L, const BatchSet S) {
+  stage_batch_body<N, Real>(L, S);
 }
 
 template <int N, typename Real>
 constexpr void (*stage_batch_kernel_ptr())(const BatchLaunch, const BatchSet) {
-  if constexpr (N == 5 && std::is_same<Real, float>::value) {
-    return &stage_batch_kernel_n5<float>;
+  if constexpr ((N == 3 || N == 5) && std::is_same<Real, float>::value) {
+    return &stage_batch_kernel_bounded<N, Real, 5>;
   } else {
     return &stage_batch_kernel<N, Real>;
   }
