@@ -10,10 +10,12 @@
 //      and vol = -1/2 * (1/J) * acc, with A(m)u = -(sigma m, Voigt(sym(m (x) v))).
 //      A is linear in m, so along the line through node a both parts are
 //      sum_b A(D_ab (Ja^i_a + Ja^i_b)) u_b, accumulated from the state and
-//      metric tiles (no staging, no barrier between directions).
+//      metric tiles (no staging, no barrier between directions); FP64 from
+//      N = 6 on stages A(Ja^i)u instead, which takes fewer FP64 operations.
 //   3. Face items (EPB*6*nf of them, spread over all threads): own trace from
-//      smem, neighbour trace from HBM/L2 through the neighbour map (or the
-//      boundary ghost), flux difference 1/2 (A(m) - tau S(m))(u^- - u^+) with
+//      smem, neighbour trace from HBM/L2 through the neighbour map (FP32 tiles
+//      of several elements: from smem when the neighbour is in the tile) or
+//      the boundary ghost, flux difference 1/2 (A(m) - tau S(m))(u^- - u^+) with
 //      m = n sJ the scaled outward normal and S(m) = sJ Q|Q^{-1}A(n)| the
 //      impedance-weighted upwind stabilisation of the face medium -- the upwind
 //      HDG flux of eq. RiemannFluxBoth (for the flux matrix Q^{-1}A(n)) with the
