@@ -612,7 +612,7 @@ def run_ihdg(args):
         implicit.append({"cfl": cfl, "dt": dt, "steps": args.ihdg_steps, "iterations_per_step": counts,
                          "ms_per_step": wall * 1e3 / args.ihdg_steps})
         s.close()
-    # shallow water, Crank-Nicolson (the paper's Section 6.3 table: 32 x 32 elements, p = 2)
+    # shallow water, Crank-Nicolson (the paper's Section 6.2 table: 32 x 32 elements, p = 2)
     Ns, Es = 2, 32
     rs, _ = reference_nodes(Ns)
     mesh = wl.structured_hex_mesh((Es, Es, 1), (False, False, True),

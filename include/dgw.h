@@ -9,10 +9,10 @@
  * medium in Q; the hot path), scalar transport (m = 1, A_k = beta_k, Q = 1;
  * Section 6.1) and the linearized shallow-water system of
  * eq. linearizedShallow with Phi = 1 and no Coriolis force, friction or wind
- * stress (m = 3, u = (phi, Phi u, Phi v), Q = I, A_3 = 0; Section 6.3).  The numerical flux is the upwind HDG flux (eq. RiemannFluxBoth)
+ * stress (m = 3, u = (phi, Phi u, Phi v), Q = I, A_3 = 0; Section 6.2).  The numerical flux is the upwind HDG flux (eq. RiemannFluxBoth)
  * with the trace eliminated through the face conservation condition
  * (eq. HDGeqn, in the form of eq. iHDGtrace); the time scheme is the paper's
- * element-by-element explicit HDG scheme (Section 4.2) with LSRK(5,4) in place
+ * element-by-element explicit HDG scheme (Section 4.3) with LSRK(5,4) in place
  * of forward Euler.
  *
  * Conventions shared by every call
@@ -134,13 +134,15 @@ dgw_status dgw_material_upload(dgw_ctx* ctx, const double* rho, const double* la
 
 /* rhs = L(u) = Q^{-1} [ split-form volume term + lifted upwind flux
  * difference ] for every element (the explicit HDG right-hand side, Section
- * 4.2, with the flux of eq. RiemannFluxBoth).  u: [9][nel][Np] input, rhs:
+ * 4.3, with the flux of eq. RiemannFluxBoth).  u: [9][nel][Np] input, rhs:
  * [9][nel][Np] output, both FP64, must not overlap.  t is the stage time (no
  * time-dependent terms are active; kept for sources). */
 dgw_status dgw_rhs(dgw_ctx* ctx, const double* u, double* rhs, double t, void* stream);
 
 /* One fused LSRK stage s (0..4):  res <- a_s res + dt L(u_in);
- * u_out <- u_in + b_s res.  u_in and u_out must be distinct buffers (the
+ * u_out <- u_in + b_s res (the explicit HDG scheme of Section 4.3, with the
+ * five-stage low-storage Runge-Kutta method of Carpenter and Kennedy in place
+ * of forward Euler).  u_in and u_out must be distinct buffers (the
  * face gather reads neighbours of u_in while u_out is written); res is read
  * and written in place.  Device pointers only. */
 dgw_status dgw_stage(dgw_ctx* ctx, const double* u_in, double* u_out, double* res, int stage,
@@ -154,7 +156,8 @@ dgw_status dgw_stage(dgw_ctx* ctx, const double* u_in, double* u_out, double* re
 dgw_status dgw_stage_energy(dgw_ctx* ctx, const double* u_in, double* u_out, double* res, int stage,
                             double t, double dt, double* energy_out, void* stream);
 
-/* nsteps LSRK(5,4) steps of size dt from time t0, in place on u and res.
+/* nsteps LSRK(5,4) steps of size dt from time t0, in place on u and res
+ * (the explicit scheme of Section 4.3, five dgw_stage calls per step).
  * The first stage does not read the register (a_0 = 0), so the incoming
  * contents of res never matter; on return res holds the register of the last
  * stage.  res may be NULL: the context keeps the register in its own device
@@ -167,8 +170,9 @@ dgw_status dgw_step(dgw_ctx* ctx, double* u, double* res, double t0, double dt, 
                     void* stream);
 
 /* dgw_step whose last stage also accumulates the discrete energy of the new
- * state (as dgw_stage_energy), so advancing a state and reading its energy
- * costs no second pass over it; with host buffers, no second upload.
+ * state (as dgw_stage_energy; E as in dgw_energy), so advancing a state and
+ * reading its energy costs no second pass over it; with host buffers, no
+ * second upload.
  * nsteps >= 1; energy_out: host double; synchronises `stream`.
  * DGW_ERR_UNSTABLE if the energy is not finite. */
 dgw_status dgw_step_energy(dgw_ctx* ctx, double* u, double* res, double t0, double dt, int nsteps,
@@ -300,11 +304,11 @@ dgw_status dgw_energy_static(int N, int64_t nel, const double* x, const double* 
  * neighbours' at k in the weighted trace,
  *     (sigma I - L_K^self) u_K^{k+1} = b_K + L_K^nbr(u^k),
  * L_K^self being L with the interior neighbour states zero.  Transport:
- * sigma = 0 is the steady equation (Section 3.1, forcing f); sigma = 1/dt
+ * sigma = 0 is the steady equation (Section 4.1, forcing f); sigma = 1/dt
  * with b = u^m/dt + f is one implicit Euler step solved element by element
- * (Section 3.3, the locally implicit method).  Shallow water: sigma = 2/dt
+ * (Section 4.3, the locally implicit method).  Shallow water: sigma = 2/dt
  * with b = sigma u^m + L(u^m) (f = dgw_rhs of u^m) is one Crank-Nicolson
- * step (Section 6.3).  Elastic (FP64 contexts): sigma = 1/dt with
+ * step (Section 6.2).  Elastic (FP64 contexts): sigma = 1/dt with
  * b = u^m/dt + f is one implicit Euler step, sigma = 2/dt with
  * b = sigma u^m + L(u^m) one Crank-Nicolson step, of du/dt = L(u) (L includes
  * Q^{-1}); a point force enters through f.  Degrees: transport N <= 4, shallow

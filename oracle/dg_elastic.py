@@ -19,7 +19,7 @@ deliberately slow and follows the method step by step:
   condition (Section 2, eq. HDGeqn) in the form of Section 3, eq. iHDGtrace,
   with both sides at the same time level, and the HDG flux
   F_hat.n = A(n)u + |A|(u - u_hat) follows (eq. RiemannFluxBoth).
-* The element-by-element explicit scheme of Section 4.2 ("iHDG as a locally
+* The element-by-element explicit scheme of Section 4.3 ("iHDG as a locally
   implicit method": explicit HDG with forward Euler) is advanced here with a
   five-stage low-storage Runge-Kutta method instead of forward Euler.
 

@@ -12,7 +12,7 @@ A_k, Q = I and C = 0.  Two instances from the paper's numerical sections:
   Section 6.1);
 * linearized shallow water: m = 3, u = (phi, Phi u, Phi v), A_1 and A_2 of
   eq. linearizedShallow with Phi = 1, no Coriolis force, friction or wind
-  stress (the setting of the standing-wave test, Section 6.3); the 2-D
+  stress (the setting of the standing-wave test, Section 6.2); the 2-D
   problem is posed on a mesh one element thick in z with periodic z faces,
   and A_3 = 0.
 

@@ -6,14 +6,14 @@ TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and
 
 The problem is  sigma u - L(u) = b  with L the semi-discrete operator of
 ``FriedrichsDG`` (upwind flux, trace eliminated) and b given; for transport:
-* sigma = 0, b = f: the steady transport equation (Section 3.1,
+* sigma = 0, b = f: the steady transport equation (Section 4.1,
   eq. transport) with forcing f;
 * sigma = 1/dt, b = u^m / dt + f: one implicit Euler step of the
-  time-dependent transport equation (Section 3.3, eq. implicitHDG), of which
-  iHDG-II is the locally implicit solver (Section 3.3);
+  time-dependent transport equation (Section 4.2; eq. implicitHDG, Section 4.3), of which
+  iHDG-II is the locally implicit solver (Section 4.3);
 and for the shallow-water system sigma = 2/dt, b = sigma u^m + L(u^m): one
 Crank-Nicolson step, the time scheme of the paper's shallow-water test
-(Section 6.3).
+(Section 6.2).
 
 iHDG-II, iteration k -> k+1 (eqs. iHDGlocal and iHDGtrace): every element K
 solves its local problem with its own unknowns at k+1 and its neighbours'

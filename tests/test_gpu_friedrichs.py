@@ -6,7 +6,7 @@ against the oracle's FriedrichsDG, through the C ABI.
 * each fused LSRK stage, a full step and the energies (separate and fused):
   <= 1e-12;
 * the whole path at larger sizes against the paper's exact standing wave
-  (Section 6.3): design-order convergence of the GPU result;
+  (Section 6.2): design-order convergence of the GPU result;
 * elastic-only calls and undefined boundary tags are refused.
 """
 import ctypes
@@ -112,7 +112,7 @@ def test_stages_step_and_energy_parity(system, E):
 
 
 def test_standing_wave_converges_at_design_order_on_the_gpu():
-    """The paper's shallow-water standing wave with walls (Section 6.3), N = 3,
+    """The paper's shallow-water standing wave with walls (Section 6.2), N = 3,
     run on the GPU to T = 0.25 on 4 x 4 and 16 x 16 meshes (the oracle's pin
     covers 4 -> 8); the error against the exact solution falls at >= N + 1 - 0.4."""
     import torch

@@ -173,7 +173,7 @@ def test_refusals():
     assert capi.dgw_ihdg_setup(el._ctx, 0.0, None) == -2          # elastic: mesh first
 
 
-# ---- shallow water, Crank-Nicolson (Section 6.3) ------------------------------
+# ---- shallow water, Crank-Nicolson (Section 6.2) ------------------------------
 
 SW_GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "ihdg_shallow_water_iterations.txt")
 

@@ -9,7 +9,7 @@ What fixes each part without a reference implementation:
   with walls, brute-force skew-symmetry / dissipativity of the assembled operator;
 * everything together: design-order convergence to the exact solutions of the
   paper's transport (periodic stand-in, Section 6.1) and shallow-water
-  standing-wave (Section 6.3) tests.
+  standing-wave (Section 6.2) tests.
 """
 import numpy as np
 import pytest
@@ -161,7 +161,7 @@ def test_transport_design_order(N, meshes, min_rate):
 
 @pytest.mark.parametrize("N,meshes,min_rate", [(2, (4, 8), 2.8), (3, (4, 8), 3.6)])
 def test_shallow_water_standing_wave_design_order(N, meshes, min_rate):
-    """The paper's standing wave with walls (Section 6.3): design rate N + 1."""
+    """The paper's standing wave with walls (Section 6.2): design rate N + 1."""
     T = 0.25
     errs = []
     for E in meshes:

@@ -10,7 +10,7 @@
 * the iteration counts of the paper's table (golden fixture), with its
   stopping criterion (eq. tolerancecriteria): within one iteration, and the
   asymptotics d N_el^(1/d);
-* the locally implicit use (Section 3.3): one implicit Euler step solved by
+* the locally implicit use (Section 4.3): one implicit Euler step solved by
   iHDG-II equals the direct implicit step.
 """
 import os
@@ -110,7 +110,7 @@ def test_locally_implicit_step_equals_the_direct_implicit_step():
     assert ih.norm(u - ud) < 1e-10 * ih.norm(ud)
 
 
-# ---- the linearized shallow-water system, Crank-Nicolson (Section 6.3) -------
+# ---- the linearized shallow-water system, Crank-Nicolson (Section 6.2) -------
 
 SW_GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "ihdg_shallow_water_iterations.txt")
 

@@ -70,7 +70,7 @@ def transport_gaussian(x, t=0.0, shift=0.35):
 
 
 def shallow_water_standing_wave(x, t=0.0):
-    """The linear standing wave of the paper's shallow-water test (Section 6.3,
+    """The linear standing wave of the paper's shallow-water test (Section 6.2,
     Phi = 1, f = gamma = 0, no wind stress) on [0,1]^2 with walls:
     phi = cos(pi x) cos(pi y) cos(sqrt2 pi t),
     u = sin(pi x) cos(pi y) sin(sqrt2 pi t) / sqrt2,
