@@ -228,3 +228,19 @@ def test_elastic_crank_nicolson_by_ihdg_energy_identity():
     assert hist[-1] < 1e-13
     E0, E1 = op.energy(u0), op.energy(u)
     assert abs((E1 - E0) - 0.25 * dt * op.energy_rate(u + u0)) < 1e-11 * E0
+
+
+def test_elastic_crank_nicolson_identity_at_degree_two():
+    """The Crank-Nicolson energy identity at N = 2 (243-row local blocks), and
+    the converged iterate equals the direct step."""
+    from oracle.ihdg import IHDG
+    op, x, dt0 = _el_op(E=(3, 2, 2), N=2, seed=5)
+    dt = 4.0 * dt0
+    ih = IHDG(op, 2.0 / dt)
+    u0 = wl.random_fields(9, op.nel, op.Np, 13)
+    b = ih.sigma * u0 + op.rhs(u0, source=False)
+    u, its, hist = ih.solve(b, u0, tol=1e-13, max_iter=400)
+    assert hist[-1] < 1e-13
+    E0, E1 = op.energy(u0), op.energy(u)
+    assert abs((E1 - E0) - 0.25 * dt * op.energy_rate(u + u0)) < 1e-11 * E0
+    assert ih.norm(u - ih.direct(b)) < 1e-10 * ih.norm(u)
