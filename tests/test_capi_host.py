@@ -105,3 +105,19 @@ def test_calls_on_null_context_fail_cleanly(lib):
     assert capi.dgw_step_energy(None, None, None, 0.0, 0.1, 1, None)[0] == -1
     assert capi.dgw_mesh_upload(None, 1, None, None, None, None, None) == -1
     assert capi.dgw_destroy(None) == 0
+
+
+def test_every_declaration_is_documented():
+    """Each function of the boundary is preceded by its own comment block
+    (argument meaning, layout, ownership, errors)."""
+    text = open(os.path.join(ROOT, "include", "dgw.h")).read()
+    undocumented = []
+    for m in re.finditer(r"^(?:dgw_status|const char\*|int)\s+(dgw_\w+)\s*\(", text, re.M):
+        lines = text[:m.start()].rstrip().split("\n")
+        while lines and lines[-1].lstrip().startswith("#"):      # a #define between comment and call
+            lines.pop()
+        if not "\n".join(lines).rstrip().endswith("*/"):
+            undocumented.append(m.group(1))
+    # calls documented together with the call right above them
+    grouped = {"dgw_destroy", "dgw_batch_destroy", "dgw_batch_last_error", "dgw_abi_version"}
+    assert not [f for f in undocumented if f not in grouped], undocumented
