@@ -60,7 +60,7 @@ def measured_traffic(precision):
     import hashlib
     csrc = os.path.join(ROOT, "paper_1711_01175_gb300", "csrc")
     h = hashlib.sha256()
-    for f in ("dgw_stage.cuh", "dgw_internal.cuh", "dgw_stage_fp64.cu", "dgw_stage_mixed.cu"):
+    for f in ("dgw_stage.cuh", "dgw_internal.cuh", "dgw_stage_fp64.cu", "dgw_stage_mixed.cu", "dgw_stage_mixed_tc.cu"):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     path = os.path.join(ROOT, "profiles", "stage_kernel_traffic.txt")
@@ -266,6 +266,54 @@ def run_variant(precision, cfg, data, steps, warmup, device, stream, clocks=None
     del ua, ub, res
     s.close()
     torch.cuda.empty_cache()
+    return out
+
+
+VARIANT_DTYPE = {"fp64": "f64", "mixed": "f32/f64", "mixed_tc": "f16x2(tensor)/f32/f64",
+                 "mixed_tc_bf16": "bf16x2(tensor)/f32/f64"}
+VOLUME_FORM = {"mixed": "FP32 CUDA cores",
+               "mixed_tc": "D contractions on tensor cores, FP16 hi/lo (per-row 2^k scale), FP32 accumulate",
+               "mixed_tc_bf16": "D contractions on tensor cores, BF16 hi/lo, FP32 accumulate"}
+
+
+def mixed_roofline(prec, N, r, hbm_peak, peak_kind, cfg):
+    """HBM roofline of a mixed-path stage kernel: the algorithmic bytes of the
+    step's five launches (stage 0 reads no register) over the CUDA-event stage
+    time, against the copy bandwidth."""
+    nbytes = step_bytes_per_dof(N, 4) * r["dof"] / 5.0      # average per launch
+    ach = nbytes / (r["stage_ms"] * 1e-3) / 1e9
+    vol = {"mixed": "", "mixed_tc": ",TcFp16", "mixed_tc_bf16": ",TcBf16"}[prec]
+    return {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+            "traffic": measured_traffic(prec) if cfg.name == "large-64^3-N4" else None,
+            "kernel": f"stage_kernel<{N},float,LSRK{vol}>",
+            "note": f"algorithmic bytes {step_bytes_per_dof(N, 4) / 5:.2f} B/DOF per launch "
+                    f"(stage 0: {algorithmic_bytes_per_dof(N, 4, True):.2f}, stages 1-4: "
+                    f"{algorithmic_bytes_per_dof(N, 4):.2f}); peak {peak_kind} copy bandwidth; volume term: "
+                    f"{VOLUME_FORM[prec]}"}
+
+
+def run_ab_precision(args, device, stream, hbm_peak, peak_kind):
+    """A/B of the volume forms on the precision workload (48^3, N=7): FP64,
+    mixed with the FP32 CUDA-core volume term, and the two tensor-core forms,
+    each timed over the same LSRK steps as the headline (device-resident
+    inputs, CUDA events)."""
+    cfg, data = build_workload("precision")
+    out = {"workload": workload_name(cfg), "dof": data["mesh"].nel * (cfg.N + 1) ** 3 * 9}
+    for prec in ("fp64", "mixed", "mixed_tc", "mixed_tc_bf16"):
+        k = max(2, args.ab_steps // 4) if prec == "fp64" else args.ab_steps
+        r = run_variant(prec, cfg, data, k, args.warmup, device, stream, Clocks(device.index or 0))
+        v = {"value": r["dof"] * 5 * k / (r["total_ms"] * 1e-3), "steps": k, "ms_per_step": r["total_ms"] / k,
+             "stage_ms": r["stage_ms"], "dtype": VARIANT_DTYPE[prec], "clocks": r["clocks"]}
+        if prec == "fp64":
+            flops = algorithmic_flops_per_element(cfg.N) * r["nel"]
+            v["roofline"] = {"bound": "alu", "achieved": flops / (r["stage_ms"] * 1e-3) / 1e12,
+                             "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s"}
+            v["roofline"]["frac"] = v["roofline"]["achieved"] / FP64_PEAK_TFLOPS
+        else:
+            v["roofline"] = mixed_roofline(prec, cfg.N, r, hbm_peak, peak_kind, cfg)
+        out[prec] = v
+    best = max(("mixed", "mixed_tc", "mixed_tc_bf16"), key=lambda q: out[q]["value"])
+    out["fastest_mixed_form"] = best
     return out
 
 
@@ -699,11 +747,15 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--precision", default="both", choices=["both", "fp64", "mixed"])
+    ap.add_argument("--precision", default="all", choices=["all", "both", "fp64", "mixed", "mixed_tc", "mixed_tc_bf16"],
+                    help="all: FP64 headline plus the mixed CUDA-core and tensor-core variants; both: FP64 and mixed")
     ap.add_argument("--workload", default="large", choices=["large", "precision"],
                     help="large: 64^3, N=4 (the metric's workload); precision: 48^3, N=7")
     ap.add_argument("--elements", type=int, default=None, help="elements per axis (default: the workload's)")
-    ap.add_argument("--mixed-steps", type=int, default=None, help="steps for the mixed variant (default 4x)")
+    ap.add_argument("--mixed-steps", type=int, default=None, help="steps for the mixed variants (default 4x)")
+    ap.add_argument("--no-ab", action="store_true",
+                    help="skip the A/B of the volume forms on the 48^3, N=7 precision workload")
+    ap.add_argument("--ab-steps", type=int, default=8, help="steps per variant of that A/B")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=256, help="elements per reference-arm step")
@@ -756,7 +808,8 @@ def main():
 
     cfg, data = build_workload(args.workload, args.elements)
     hbm_peak, peak_kind = peaks()
-    variants = ["fp64", "mixed"] if args.precision == "both" else [args.precision]
+    variants = {"all": ["fp64", "mixed", "mixed_tc", "mixed_tc_bf16"], "both": ["fp64", "mixed"]}.get(
+        args.precision, [args.precision])
     results = {}
     for prec in variants:
         k = args.steps if prec == "fp64" else (args.mixed_steps or 4 * args.steps)
@@ -764,7 +817,7 @@ def main():
         r = run_variant(prec, cfg, data, k, args.warmup, device, stream, clk)
         r["steps"] = k
         r["value"], r["max_ms"] = whole_job_rate(r["total_ms"], r["dof"] * 5 * k, device)
-        if not args.no_e2e:
+        if not args.no_e2e and prec != "mixed_tc_bf16":
             e = run_e2e(prec, cfg, data, max(2, k // 4), args.warmup, device, stream)
             r["e2e"] = {"value": r["dof"] * 5 * max(2, k // 4) / (e["ms"] * 1e-3) * world, "unit": UNIT,
                         "h2d_bytes_per_step": e["h2d_bytes_per_step"],
@@ -784,27 +837,19 @@ def main():
                              "note": "FP64 flops as written per launch / CUDA-event stage time; peak derived "
                                      "from 152 SMs x 2 DFMA/clk x 2.07 GHz (nominal)"}
         else:
-            nbytes = step_bytes_per_dof(N, 4) * r["dof"] / 5.0      # average per launch
-            ach = nbytes / (r["stage_ms"] * 1e-3) / 1e9
-            r["roofline"] = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                             "frac": ach / hbm_peak,
-                             "traffic": measured_traffic("mixed") if cfg.name == "large-64^3-N4" else None,
-                             "kernel": f"stage_kernel<{N},float,LSRK>",
-                             "note": f"algorithmic bytes {step_bytes_per_dof(N, 4) / 5:.2f} B/DOF per launch "
-                                     f"(stage 0: {algorithmic_bytes_per_dof(N, 4, True):.2f}, stages 1-4: "
-                                     f"{algorithmic_bytes_per_dof(N, 4):.2f}); peak {peak_kind} copy bandwidth"}
+            r["roofline"] = mixed_roofline(prec, N, r, hbm_peak, peak_kind, cfg)
         results[prec] = r
 
     if rank != 0:
         torch.distributed.destroy_process_group() if world > 1 else None
         return
-    head = results.get("fp64") or results["mixed"]
-    head_prec = "fp64" if "fp64" in results else "mixed"
+    head_prec = "fp64" if "fp64" in results else next(iter(results))
+    head = results[head_prec]
     line = {
         "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": head["steps"],
         "warmup": args.warmup, "ms_per_step": head["max_ms"] / head["steps"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if head_prec == "fp64" else "f32/f64",
+        "dtype": VARIANT_DTYPE[head_prec],
         "data": "synthetic (seeded mesh, medium and Gaussian pulse of the large workload)",
         "config": {"workload": workload_name(cfg), "precision": head_prec, "elements": head["nel"],
                    "dof": head["dof"], "step": "one LSRK(5,4) step: 5 fused stage launches, the last one also accumulating the energy of the new state",
@@ -828,11 +873,16 @@ def main():
     if world == 1 and not args.no_ihdg:
         line["ihdg"] = run_ihdg(args)
     if len(results) > 1:
-        m = results["mixed"]
-        line["variants"] = {"mixed": {"value": m["value"], "dtype": "f32/f64", "steps": m["steps"],
+        line["variants"] = {}
+        for prec, m in results.items():
+            if prec == head_prec:
+                continue
+            line["variants"][prec] = {"value": m["value"], "dtype": VARIANT_DTYPE[prec], "steps": m["steps"],
                                       "ms_per_step": m["max_ms"] / m["steps"], "roofline": m["roofline"],
                                       "clocks": m["clocks"], "e2e": m.get("e2e"),
-                                      "gpu_launches": m["gpu_launches"]}}
+                                      "gpu_launches": m["gpu_launches"]}
+    if world == 1 and not args.no_ab and args.workload == "large" and args.precision == "all":
+        line["ab_precision_workload"] = run_ab_precision(args, device, stream, hbm_peak, peak_kind)
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

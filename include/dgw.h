@@ -57,7 +57,7 @@ typedef enum {
   DGW_ERR_UNSUPPORTED = -7  /* configuration or call not built */
 } dgw_status;
 
-enum { DGW_PRECISION_FP64 = 0, DGW_PRECISION_MIXED = 1 };
+enum { DGW_PRECISION_FP64 = 0, DGW_PRECISION_MIXED = 1, DGW_PRECISION_MIXED_TC_FP16 = 2, DGW_PRECISION_MIXED_TC_BF16 = 3 };
 /* Boundary tags.  1 is the traction-free surface of the elastic system
  * (exterior state (v, -sigma)) and the reflecting wall of the shallow-water
  * system (exterior state (phi, q - 2 (q.n) n), q the momentum, n the
@@ -73,7 +73,13 @@ typedef struct {
   int precision;  /* DGW_PRECISION_FP64: every operation in FP64.
                      DGW_PRECISION_MIXED: volume, flux and lift in FP32 with FP32
                      geometry; the Runge-Kutta registers and energy stay FP64.
-                     Elastic system only. */
+                     DGW_PRECISION_MIXED_TC_FP16 / _BF16: as MIXED, with the
+                     volume term's 1-D derivative contractions D u and
+                     D (A(Ja^i) u) on the tensor cores: each operand split into
+                     a 16-bit hi and lo part (FP16 with a power-of-two scale per
+                     line group, or BF16), D_hi x_hi + D_hi x_lo + D_lo x_hi
+                     accumulated in FP32.  Single solves only (not batches).
+                     The MIXED forms are for the elastic system only. */
   double cfl;     /* CFL number used by dgw_dt_cfl */
   int system;     /* DGW_SYSTEM_*.  Transport and shallow water: FP64 only, no
                      material (Q = I), no point force, receivers, adjoint or
@@ -82,7 +88,7 @@ typedef struct {
 } dgw_config;
 
 /* ABI version of this header (bumped on any signature change). */
-#define DGW_ABI_VERSION 8
+#define DGW_ABI_VERSION 9
 int dgw_abi_version(void);
 
 /* GLL nodes r[0..N] (ascending, r[0] = -1, r[N] = +1) and weights w[0..N]
@@ -288,8 +294,12 @@ const char* dgw_batch_last_error(const dgw_batch* b);
  *               `stream` (the current device's) completes.
  * Same value as dgw_energy on the same mesh to rounding.  The first call on
  * a device looks up the scratch array's device address; make that first call
- * before any stream capture.  All calls share the scratch array: calls whose
- * kernels overlap on the GPU (unordered streams) race.  Errors:
+ * before any stream capture.  The address is kept for the life of the
+ * process: it assumes the device's primary context is not destroyed
+ * (cudaDeviceReset) while the library is loaded.  All calls share the
+ * scratch array: calls whose kernels overlap on the GPU (unordered streams)
+ * race.  Every array must be device memory of the current device (or managed
+ * memory); others are refused with DGW_ERR_ARG.  Errors:
  * dgw_last_error(NULL). */
 #define DGW_ENERGY_STATIC_MAX_ELEMENTS (1 << 20)
 dgw_status dgw_energy_static(int N, int64_t nel, const double* x, const double* u, const double* rho,

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdgw.so")
 SOURCES = ["dgw_capi.cu", "dgw_batch.cu", "dgw_adjoint.cu", "dgw_geometry.cu", "dgw_energy.cu", "dgw_energy_static.cu", "dgw_stage_fp64.cu",
-           "dgw_stage_mixed.cu", "dgw_friedrichs.cu", "dgw_ihdg.cu"]
+           "dgw_stage_mixed.cu", "dgw_stage_mixed_tc.cu", "dgw_friedrichs.cu", "dgw_ihdg.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

@@ -17,6 +17,8 @@ STATUS = {0: "DGW_OK", -1: "DGW_ERR_ARG", -2: "DGW_ERR_STATE", -3: "DGW_ERR_OOM"
           -5: "DGW_ERR_UNSTABLE", -6: "DGW_ERR_TIMEOUT", -7: "DGW_ERR_UNSUPPORTED"}
 DGW_PRECISION_FP64 = 0
 DGW_PRECISION_MIXED = 1
+DGW_PRECISION_MIXED_TC_FP16 = 2
+DGW_PRECISION_MIXED_TC_BF16 = 3
 DGW_BC_INTERIOR, DGW_BC_FREE_SURFACE, DGW_BC_ABSORBING = 0, 1, 2
 DGW_BATCH_MAX_SOLVES = 128
 DGW_SYSTEM_ELASTIC, DGW_SYSTEM_TRANSPORT, DGW_SYSTEM_SHALLOW_WATER = 0, 1, 2

@@ -108,6 +108,8 @@ dgw_status dgw_batch_create(dgw_batch** out, int device, int N, int precision, i
   if (!out) return bfail(nullptr, DGW_ERR_ARG, "null argument");
   *out = nullptr;
   if (N < 1 || N > dgw::kMaxN) return bfail(nullptr, DGW_ERR_ARG, "N outside 1..7");
+  if (precision == DGW_PRECISION_MIXED_TC_FP16 || precision == DGW_PRECISION_MIXED_TC_BF16)
+    return bfail(nullptr, DGW_ERR_UNSUPPORTED, "batches run the FP64 and MIXED forms only");
   if (precision != DGW_PRECISION_FP64 && precision != DGW_PRECISION_MIXED)
     return bfail(nullptr, DGW_ERR_ARG, "unknown precision");
   if (flux_tau != 0 && flux_tau != 1) return bfail(nullptr, DGW_ERR_ARG, "flux_tau must be 0 or 1");

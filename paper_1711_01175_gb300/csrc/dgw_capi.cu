@@ -132,7 +132,8 @@ dgw_status launch_stage(dgw_ctx* c, const double* u_in, double* out, double* res
   for (int k = 0; k < 3; ++k) p.beta[k] = c->cfg.beta[k];
   cudaError_t e = c->cfg.system != DGW_SYSTEM_ELASTIC ? dgw::launch_friedrichs(c->cfg.system, c->cfg.N, lsrk, p, s)
                   : c->cfg.precision == DGW_PRECISION_MIXED ? dgw::launch_stage_mixed(c->cfg.N, lsrk, p, s)
-                                                           : dgw::launch_stage_fp64(c->cfg.N, lsrk, p, s);
+                  : c->cfg.precision == DGW_PRECISION_FP64  ? dgw::launch_stage_fp64(c->cfg.N, lsrk, p, s)
+                                                            : dgw::launch_stage_mixed_tc(c->cfg.N, c->cfg.precision, lsrk, p, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "stage kernel launch");
   return DGW_OK;
 }
@@ -245,7 +246,7 @@ dgw_status dgw_create(dgw_ctx** out, int device, const dgw_config* cfg) {
   *out = nullptr;
   if (cfg->N < 1 || cfg->N > dgw::kMaxN) return fail(nullptr, DGW_ERR_ARG, "N=%d outside 1..7", cfg->N);
   if (cfg->flux_tau != 0 && cfg->flux_tau != 1) return fail(nullptr, DGW_ERR_ARG, "flux_tau must be 0 or 1");
-  if (cfg->precision != DGW_PRECISION_FP64 && cfg->precision != DGW_PRECISION_MIXED)
+  if (cfg->precision < DGW_PRECISION_FP64 || cfg->precision > DGW_PRECISION_MIXED_TC_BF16)
     return fail(nullptr, DGW_ERR_ARG, "unknown precision %d", cfg->precision);
   if (!(cfg->cfl > 0.0)) return fail(nullptr, DGW_ERR_ARG, "cfl must be positive");
   if (cfg->system != DGW_SYSTEM_ELASTIC && cfg->system != DGW_SYSTEM_TRANSPORT &&
@@ -429,7 +430,7 @@ dgw_status dgw_mesh_upload(dgw_ctx* c, int64_t nel, const double* x, const int64
       return fail(c, DGW_ERR_ARG, "element %lld: Jacobian %.3e <= 0 at some node", (long long)e, mj[e]);
     }
   }
-  if (c->cfg.precision == DGW_PRECISION_MIXED) {
+  if (dgw::fp32_arrays(c->cfg.precision)) {
     float* g32 = nullptr;
     DGW_TRY(cudaMalloc(&g32, nodes * 10 * sizeof(float)), "alloc geometry fp32");
     c->geo = g32;
@@ -503,7 +504,7 @@ dgw_status dgw_material_upload(dgw_ctx* c, const double* rho, const double* lam,
   c->has_material = false;
   DGW_CUDA(c, cudaMalloc(&c->ec, 4 * nel * sizeof(double)), "alloc energy constants");
   DGW_CUDA(c, cudaMemcpyAsync(c->ec, ec.data(), 4 * nel * sizeof(double), cudaMemcpyHostToDevice, c->setup), "copy energy constants");
-  if (c->cfg.precision == DGW_PRECISION_MIXED) {
+  if (dgw::fp32_arrays(c->cfg.precision)) {
     std::vector<float> m32(m64.begin(), m64.end());
     std::vector<float> fz32(fz.begin(), fz.end());
     DGW_CUDA(c, cudaMalloc(&c->mat, 3 * nel * sizeof(float)), "alloc material");

@@ -120,13 +120,16 @@ energy_static_final(const double* __restrict__ partials, int nparts, double* out
   if (threadIdx.x == 0) *out = 0.5 * s;
 }
 
-bool on_device(const void* p) {
+// Where p lives: -1 not device memory, -2 managed memory (reachable from any
+// device), otherwise the ordinal of the device that holds it.
+int device_of(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return -1;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return -2;
+  return a.type == cudaMemoryTypeDevice ? a.device : -1;
 }
 
 dgw_status static_fail(dgw_status st, const std::string& msg) {
@@ -151,11 +154,18 @@ extern "C" dgw_status dgw_energy_static(int N, int64_t nel, const double* x, con
   const int Np = (N + 1) * (N + 1) * (N + 1);
   if ((double)nel * Np >= 2147483647.0) return static_fail(DGW_ERR_ARG, "dgw_energy_static: nel*Np must be below 2^31");
   const void* ptrs[] = {x, u, rho, lam, mu, energy_out};
-  for (const void* p : ptrs)
-    if (!p || !on_device(p)) return static_fail(DGW_ERR_ARG, "dgw_energy_static: every array must be device memory");
+  int where[6];
+  for (int i = 0; i < 6; ++i) {
+    where[i] = ptrs[i] ? device_of(ptrs[i]) : -1;
+    if (where[i] == -1) return static_fail(DGW_ERR_ARG, "dgw_energy_static: every array must be device memory");
+  }
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
     return static_fail(DGW_ERR_CUDA, "dgw_energy_static: no current CUDA device");
+  for (int i = 0; i < 6; ++i)
+    if (where[i] >= 0 && where[i] != dev)
+      return static_fail(DGW_ERR_ARG, "dgw_energy_static: an array is on device " + std::to_string(where[i]) +
+                                          " but device " + std::to_string(dev) + " is current");
   double* partials = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_setup_mutex);

@@ -128,6 +128,12 @@ cudaError_t launch_stage_batch(int N, bool mixed, const BatchLaunch& L, const Ba
 cudaError_t prepare_stage_batch(int N, bool mixed);
 cudaError_t launch_stage_fp64(int N, bool lsrk, const StageParams& p, cudaStream_t s);
 cudaError_t launch_stage_mixed(int N, bool lsrk, const StageParams& p, cudaStream_t s);
+// Mixed path with the volume term's derivative contractions on the tensor cores
+// (split FP16 or BF16 operands, FP32 accumulation): fmt is DGW_PRECISION_MIXED_TC_FP16
+// or DGW_PRECISION_MIXED_TC_BF16 (dgw_stage_mixed_tc.cu).
+cudaError_t launch_stage_mixed_tc(int N, int fmt, bool lsrk, const StageParams& p, cudaStream_t s);
+// Precisions whose geometry, face and material arrays are FP32.
+inline bool fp32_arrays(int precision) { return precision != DGW_PRECISION_FP64; }
 cudaError_t launch_stage_adjoint(int N, int mode, const StageParams& p, cudaStream_t s);   // mode 2: ADJ, 3: GRAD
 void stage_shape(int N, int* epb, int* threads);
 

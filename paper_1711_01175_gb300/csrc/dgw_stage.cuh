@@ -30,6 +30,9 @@
 #include <atomic>
 #include <type_traits>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "dgw_internal.cuh"
 
 namespace dgw {
@@ -178,17 +181,49 @@ __host__ __device__ constexpr bool staged_volume() {
   return std::is_same<Real, double>::value && N >= 6;
 }
 
-template <int N, typename Real>
+// Volume-term arithmetic of the FP32 path: CUDA cores (the combined form), or
+// the derivative contractions on the tensor cores with split operands.
+enum { kVolCuda = 0, kVolTcFp16 = 1, kVolTcBf16 = 2 };
+
+// Tensor-core volume form (FP32 path).  Along direction i the conservative and
+// non-conservative parts need the contractions D_i u and D_i F, F = A_+(Ja^i) u,
+// of 18 fields.  Their lines of n values are laid out line-major in shared memory
+// with a pitch of P >= n floats (a power of two; positions n..P-1 are zero), so
+// that one 8-float row holds SEG = 8/P lines and 16 rows form the A operand of
+// one mma.sync.m16n8k8 (FP32 accumulation) whose B operand is the block-diagonal
+// matrix of SEG copies of D^T.  Each field occupies FS floats (whole 32-word
+// blocks), and within a field a pair of positions (2t, 2t+1) is stored at pair
+// slot t ^ h(block) of its row, which spreads the node-wise writes of the three
+// directions over the banks while each half-warp still reads 32 distinct words.
+template <int N>
+struct TcShape {
+  using S = Shape<N>;
+  static constexpr int n = S::n;
+  static constexpr int P = n <= 2 ? 2 : (n <= 4 ? 4 : 8);
+  static constexpr int SEG = 8 / P;
+  static constexpr int L = S::EPB * S::nf;                 // lines per field and direction
+  static constexpr int FS = ((L * P + 31) / 32) * 32;      // floats per field
+  static constexpr int FSB = FS / 32;                      // 32-word blocks per field
+  static constexpr int TILES = (18 * FS + 127) / 128;      // 16 x 8 tiles per direction
+  static constexpr int WORDS = TILES * 128;
+  static constexpr bool ZERO = P > n || FS > L * P;        // padding to clear once per CTA
+};
+
+__device__ __forceinline__ int tc_swz(int block) { return ((block & 1) << 1) | ((block >> 1) & 1); }
+
+template <int N, typename Real, int VOL = kVolCuda>
 struct StageSmem {
   using S = Shape<N>;
   static constexpr int PK = Pack<Real>::PK;
   static constexpr size_t u_off = 0;                                    // Real [NTILE][PK] state
   // Real [9][NFACE_ITEMS] face fluxes; the staged volume form first keeps
-  // A_+(Ja^i)u [NTILE][PK] of one direction in the same region.
+  // A_+(Ja^i)u [NTILE][PK] of one direction in the same region, the tensor-core
+  // form its line-major operands.
   static constexpr size_t f_off = u_off + sizeof(Real) * S::NTILE * PK;
-  static constexpr size_t fwords = (staged_volume<N, Real>() && S::NTILE * PK > 9 * S::NFACE_ITEMS)
-                                       ? S::NTILE * PK
-                                       : 9 * S::NFACE_ITEMS;
+  static constexpr size_t fwords0 = (staged_volume<N, Real>() && S::NTILE * PK > 9 * S::NFACE_ITEMS)
+                                        ? S::NTILE * PK
+                                        : 9 * S::NFACE_ITEMS;
+  static constexpr size_t fwords = (VOL != kVolCuda && TcShape<N>::WORDS > fwords0) ? TcShape<N>::WORDS : fwords0;
   static constexpr size_t fbytes = sizeof(Real) * fwords;
   static constexpr size_t g_off = f_off + ((fbytes + 15) / 16) * 16;     // Real [NTILE][PK] Ja, 1/J
   static constexpr size_t d_off = g_off + sizeof(Real) * S::NTILE * PK;  // Real [n*n]
@@ -208,6 +243,113 @@ __host__ __device__ constexpr int gslot_ij() {
   return std::is_same<Real, float>::value ? 3 : 9;
 }
 
+// ---- tensor-core volume form (FP32 path) -----------------------------------
+// Split x into hi + lo in the 16-bit format: hi = round(x), lo = round(x - hi),
+// two values packed per 32-bit register (the first in the low half).
+template <int VOL>
+__device__ __forceinline__ void tc_split(float x0, float x1, unsigned& hi, unsigned& lo) {
+  if constexpr (VOL == kVolTcFp16) {
+    const __half2 h = __floats2half2_rn(x0, x1);
+    const float2 f = __half22float2(h);
+    const __half2 l = __floats2half2_rn(x0 - f.x, x1 - f.y);
+    hi = *reinterpret_cast<const unsigned*>(&h);
+    lo = *reinterpret_cast<const unsigned*>(&l);
+  } else {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+    const unsigned hb = *reinterpret_cast<const unsigned*>(&h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - __uint_as_float(hb << 16), x1 - __uint_as_float(hb & 0xffff0000u));
+    hi = hb;
+    lo = *reinterpret_cast<const unsigned*>(&l);
+  }
+}
+
+// c += A B for one m16n8k8 tile: A 16 x 8 (a01: row g, a23: row g + 8), B 8 x 8.
+template <int VOL>
+__device__ __forceinline__ void tc_mma(float (&c)[4], unsigned a01, unsigned a23, unsigned b) {
+  if constexpr (VOL == kVolTcFp16) {
+    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%0,%1,%2,%3};\n"
+                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+                 : "r"(a01), "r"(a23), "r"(b));
+  } else {
+    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%0,%1,%2,%3};\n"
+                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+                 : "r"(a01), "r"(a23), "r"(b));
+  }
+}
+
+// This thread's B fragment (rows k = 2t, 2t+1 of column g) of the block-diagonal
+// B with B[k][a] = D[a][k] inside each P x P block, split into hi and lo.  The
+// entries of D are O(1) to O(N^2): no scaling is needed in either format.
+template <int N, int VOL>
+__device__ __forceinline__ void tc_b_fragment(const float* D_s, unsigned& bhi, unsigned& blo) {
+  using T = TcShape<N>;
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  float v[2];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const int k = 2 * t + j;
+    const bool in = (k / T::P == g / T::P) && (k % T::P) < T::n && (g % T::P) < T::n;
+    v[j] = in ? D_s[(g % T::P) * T::n + (k % T::P)] : 0.f;
+  }
+  tc_split<VOL>(v[0], v[1], bhi, blo);
+}
+
+// Field-local word of (line l, position b) of one direction's operands.
+template <int N>
+__device__ __forceinline__ int tc_word(int l, int b) {
+  const int w = l * TcShape<N>::P + b;
+  return w ^ (tc_swz(w >> 5) << 1);
+}
+
+// The contractions of one direction, in place: every warp takes 16 x 8 tiles
+// of the operand region and replaces each row's lines x by D x.  FP16: each row
+// is scaled by the power of two 2^s that brings its largest magnitude into
+// [2^14, 2^15) (the exponent maximum over the four threads of the row's quad;
+// s <= 126 so that 2^-s is a normal float, which leaves rows below 2^-112 one
+// bit of headroom short); the products hi*hi + hi*lo + lo*hi are exact and
+// summed in FP32, and the result is scaled back by 2^-s.  BF16 keeps the FP32
+// exponent range and needs no scaling.
+template <int N, int VOL>
+__device__ __forceinline__ void tc_contract(float* X, unsigned bhi, unsigned blo) {
+  using T = TcShape<N>;
+  constexpr int NW = Shape<N>::NT / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  for (int tile = warp; tile < T::TILES; tile += NW) {
+    const int blk0 = 4 * tile + (g >> 2), blk1 = blk0 + 2;     // 32-word blocks of rows g and g + 8
+    float* p0 = X + tile * 128 + g * 8 + 2 * (t ^ tc_swz(blk0 % T::FSB));
+    float* p1 = X + tile * 128 + (g + 8) * 8 + 2 * (t ^ tc_swz(blk1 % T::FSB));
+    float2 x0 = *reinterpret_cast<const float2*>(p0);
+    float2 x1 = *reinterpret_cast<const float2*>(p1);
+    float inv0 = 1.f, inv1 = 1.f;
+    if constexpr (VOL == kVolTcFp16) {
+      const unsigned m0 = max(__float_as_uint(fabsf(x0.x)), __float_as_uint(fabsf(x0.y)));
+      const unsigned m1 = max(__float_as_uint(fabsf(x1.x)), __float_as_uint(fabsf(x1.y)));
+      unsigned e = ((m0 >> 23) << 16) | (m1 >> 23);
+      e = __vmaxu2(e, __shfl_xor_sync(0xffffffffu, e, 1));
+      e = __vmaxu2(e, __shfl_xor_sync(0xffffffffu, e, 2));
+      const int s0 = min(141 - static_cast<int>(e >> 16), 126);
+      const int s1 = min(141 - static_cast<int>(e & 0xffffu), 126);
+      const float sc0 = __int_as_float((127 + s0) << 23), sc1 = __int_as_float((127 + s1) << 23);
+      inv0 = __int_as_float((127 - s0) << 23);
+      inv1 = __int_as_float((127 - s1) << 23);
+      x0.x *= sc0;
+      x0.y *= sc0;
+      x1.x *= sc1;
+      x1.y *= sc1;
+    }
+    unsigned ah0, al0, ah1, al1;
+    tc_split<VOL>(x0.x, x0.y, ah0, al0);
+    tc_split<VOL>(x1.x, x1.y, ah1, al1);
+    float c[4] = {0.f, 0.f, 0.f, 0.f};
+    tc_mma<VOL>(c, al0, al1, bhi);    // small terms first
+    tc_mma<VOL>(c, ah0, ah1, blo);
+    tc_mma<VOL>(c, ah0, ah1, bhi);
+    *reinterpret_cast<float2*>(p0) = make_float2(c[0] * inv0, c[1] * inv0);
+    *reinterpret_cast<float2*>(p1) = make_float2(c[2] * inv1, c[3] * inv1);
+  }
+}
+
 // Kernel modes.  RHS: write L(u).  LSRK: fused 2N-storage stage update.
 // ADJ: the reversed operator (A_k -> -A_k, same stabilisation) without Q^{-1}
 //   on a prepared adjoint weight z = (M Q)^{-1} w, and lu <- lu + dt w J r,
@@ -218,12 +360,14 @@ enum { kModeRhs = 0, kModeLsrk = 1, kModeAdj = 2, kModeGrad = 3 };
 
 // One tile (EPB consecutive elements) of one solve.  The caller has filled the
 // D tile of shared memory; p may live in parameter or shared memory.
-template <int N, typename Real, int MODE>
+template <int N, typename Real, int MODE, int VOL = kVolCuda>
 __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile, unsigned char* smem_raw) {
   constexpr bool LSRK = MODE == kModeLsrk;
+  static_assert(VOL == kVolCuda || (std::is_same<Real, float>::value && (MODE == kModeRhs || MODE == kModeLsrk)),
+                "the tensor-core volume form belongs to the FP32 forward path");
   const Real sgnA = MODE == kModeAdj ? Real(-1) : Real(1);
   using S = Shape<N>;
-  using L = StageSmem<N, Real>;
+  using L = StageSmem<N, Real, VOL>;
   using V = Pack<Real>;
   constexpr int n = S::n, Np = S::Np, nf = S::nf, EPB = S::EPB, NT = S::NT;
   constexpr int NTILE = S::NTILE, NFI = S::NFACE_ITEMS, PK = L::PK;
@@ -284,6 +428,7 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
     }
   }
 
+  Real uw[9];      // this node's state (kept for the tensor-core volume form)
   if (in_tile) {
     Real w[10], gj[10];
     if (active) {
@@ -296,6 +441,8 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
       for (int c = 0; c < 10; ++c) w[c] = gj[c] = 0;
     }
     w[9] = 0;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) uw[q] = w[q];
     V::store10(u_s + t * PK, w);
     if constexpr (std::is_same<Real, float>::value) {
       float4* gp = reinterpret_cast<float4*>(g_s + t * PK);
@@ -304,6 +451,13 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
       gp[2] = make_float4(gj[6], gj[7], gj[8], 0.f);
     } else {
       V::store10(g_s + t * PK, gj);
+    }
+  }
+  if constexpr (VOL != kVolCuda) {
+    if constexpr (TcShape<N>::ZERO) {
+      // zero the padding positions and lines of the operand region once
+      float4* z = reinterpret_cast<float4*>(f_s);
+      for (int i = t; i < TcShape<N>::WORDS / 4; i += NT) z[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
   }
   __syncthreads();
@@ -324,7 +478,45 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
   // accumulated term by term from the state and metric tiles (no staging, no
   // barrier between directions).  Staged form: the left-hand side, with
   // A_+(m_b) u_b staged per direction.
-  if constexpr (staged_volume<N, Real>()) {
+  if constexpr (VOL != kVolCuda) {
+    // Tensor-core form: per direction, write u and F = A_+(Ja^i) u line-major,
+    // contract all lines by D on the tensor cores, then acc += D F + A_+(Ja^i_a) D u.
+    using T = TcShape<N>;
+    float* X = reinterpret_cast<float*>(f_s);
+    unsigned bhi, blo;
+    tc_b_fragment<N, VOL>(reinterpret_cast<const float*>(D_s), bhi, blo);
+#pragma unroll 1
+    for (int dir = 0; dir < 3; ++dir) {
+      int lw = 0;
+      float4 mt = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (in_tile) {
+        const int l = el * nf + (dir == 0 ? iy + n * iz : (dir == 1 ? ix + n * iz : ix + n * iy));
+        const int b = dir == 0 ? ix : (dir == 1 ? iy : iz);
+        lw = tc_word<N>(l, b);
+        mt = reinterpret_cast<const float4*>(g_s + t * PK)[dir];
+        float F[9];
+        apply_Apos(mt.x, mt.y, mt.z, uw, F);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+          X[q * T::FS + lw] = uw[q];
+          X[(9 + q) * T::FS + lw] = F[q];
+        }
+      }
+      __syncthreads();
+      tc_contract<N, VOL>(X, bhi, blo);
+      __syncthreads();
+      if (in_tile) {
+        float du[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+          du[q] = X[q * T::FS + lw];
+          acc[q] += X[(9 + q) * T::FS + lw];
+        }
+        acc_Apos(mt.x, mt.y, mt.z, du, acc);
+      }
+      __syncthreads();    // the region is overwritten next (next direction, or the face fluxes)
+    }
+  } else if constexpr (staged_volume<N, Real>()) {
 #pragma unroll
     for (int dir = 0; dir < 3; ++dir) {
       Real m1 = 0, m2 = 0, m3 = 0;
@@ -685,17 +877,17 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
   }
 }
 
-template <int N, typename Real, int MODE>
+template <int N, typename Real, int MODE, int VOL = kVolCuda>
 __device__ __forceinline__ void stage_kernel_body(const StageParams& p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Real* D_s = reinterpret_cast<Real*>(smem_raw + StageSmem<N, Real>::d_off);
+  Real* D_s = reinterpret_cast<Real*>(smem_raw + StageSmem<N, Real, VOL>::d_off);
   for (int i = threadIdx.x; i < Shape<N>::n * Shape<N>::n; i += Shape<N>::NT) D_s[i] = to_real<Real>(p.D[i]);
-  stage_tile<N, Real, MODE>(p, blockIdx.x, smem_raw);
+  stage_tile<N, Real, MODE, VOL>(p, blockIdx.x, smem_raw);
 }
 
-template <int N, typename Real, int MODE>
+template <int N, typename Real, int MODE, int VOL = kVolCuda>
 __global__ void __launch_bounds__(Shape<N>::NT) stage_kernel(const StageParams p) {
-  stage_kernel_body<N, Real, MODE>(p);
+  stage_kernel_body<N, Real, MODE, VOL>(p);
 }
 
 // FP32 at N = 7 (512 threads): three CTAs per SM fit in shared memory but only
@@ -709,12 +901,21 @@ __global__ void __launch_bounds__(Shape<7>::NT, 3) stage_kernel_f32_n7(const Sta
   stage_kernel_body<7, float, MODE>(p);
 }
 
-template <int N, typename Real, int MODE>
+// The tensor-core form at N = 7 holds 86 KB of shared memory: two CTAs per SM,
+// which the default register allocation already allows; the bound keeps it so.
+template <int MODE, int VOL>
+__global__ void __launch_bounds__(Shape<7>::NT, 2) stage_kernel_tc_n7(const StageParams p) {
+  stage_kernel_body<7, float, MODE, VOL>(p);
+}
+
+template <int N, typename Real, int MODE, int VOL = kVolCuda>
 constexpr void (*stage_kernel_ptr())(const StageParams) {
-  if constexpr (N == 7 && std::is_same<Real, float>::value) {
+  if constexpr (N == 7 && std::is_same<Real, float>::value && VOL == kVolCuda) {
     return &stage_kernel_f32_n7<MODE>;
+  } else if constexpr (N == 7 && VOL != kVolCuda) {
+    return &stage_kernel_tc_n7<MODE, VOL>;
   } else {
-    return &stage_kernel<N, Real, MODE>;
+    return &stage_kernel<N, Real, MODE, VOL>;
   }
 }
 
@@ -846,17 +1047,17 @@ cudaError_t prepare_stage_batch_any(int N) {
   }
 }
 
-template <int N, typename Real, int MODE>
+template <int N, typename Real, int MODE, int VOL = kVolCuda>
 cudaError_t launch_stage_t(const StageParams& p, cudaStream_t s) {
   using S = Shape<N>;
-  const size_t smem = StageSmem<N, Real>::bytes;
+  const size_t smem = StageSmem<N, Real, VOL>::bytes;
   // Kernel attributes, set once per device (bit d of `ready`; devices 0..63).
   static std::atomic<unsigned long long> ready{0};
   int dev = 0;
   cudaError_t err = cudaGetDevice(&dev);
   if (err != cudaSuccess) return err;
   const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
-  constexpr auto kernel = stage_kernel_ptr<N, Real, MODE>();
+  constexpr auto kernel = stage_kernel_ptr<N, Real, MODE, VOL>();
   if (!(ready.load(std::memory_order_relaxed) & bit)) {
     err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
@@ -873,11 +1074,11 @@ cudaError_t launch_stage_t(const StageParams& p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <typename Real>
+template <typename Real, int VOL = kVolCuda>
 cudaError_t launch_stage_any(int N, bool lsrk, const StageParams& p, cudaStream_t s) {
 #define DGW_CASE(NN)                                                                   \
   case NN:                                                                             \
-    return lsrk ? launch_stage_t<NN, Real, kModeLsrk>(p, s) : launch_stage_t<NN, Real, kModeRhs>(p, s);
+    return lsrk ? launch_stage_t<NN, Real, kModeLsrk, VOL>(p, s) : launch_stage_t<NN, Real, kModeRhs, VOL>(p, s);
   switch (N) {
     DGW_CASE(1)
     DGW_CASE(2)

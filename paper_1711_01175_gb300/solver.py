@@ -43,6 +43,12 @@ def reference_nodes(N: int):
     return r, w
 
 
+# precision names -> dgw_config.precision: "mixed" FP32 volume/flux/lift on CUDA
+# cores; "mixed_tc" (FP16) and "mixed_tc_bf16" the same with the volume term's
+# derivative contractions on the tensor cores (split 16-bit operands).
+PRECISIONS = {"fp64": capi.DGW_PRECISION_FP64, "mixed": capi.DGW_PRECISION_MIXED,
+              "mixed_tc": capi.DGW_PRECISION_MIXED_TC_FP16, "mixed_tc_bf16": capi.DGW_PRECISION_MIXED_TC_BF16}
+
 SYSTEMS = {"elastic": (capi.DGW_SYSTEM_ELASTIC, 9), "transport": (capi.DGW_SYSTEM_TRANSPORT, 1),
            "shallow_water": (capi.DGW_SYSTEM_SHALLOW_WATER, 3)}
 
@@ -55,7 +61,7 @@ class Solver:
 
     def __init__(self, N: int, tau: int = 1, precision: str = "fp64", cfl: float = 0.5, device: int = 0,
                  system: str = "elastic", beta=(0.0, 0.0, 0.0)):
-        prec = {"fp64": capi.DGW_PRECISION_FP64, "mixed": capi.DGW_PRECISION_MIXED}[precision]
+        prec = PRECISIONS[precision]
         sys_id, self.m = SYSTEMS[system]
         self.system = system
         self.N, self.tau, self.precision = int(N), int(tau), precision

@@ -8,11 +8,48 @@ import numpy as np
 import oracle
 import workloads as wl
 
+# Parity bounds of the CUDA path against the oracle.
+FP64_TOL = 1e-12
+# FP32 volume/flux arithmetic on FP32 geometry: unit round-off 6e-8 times the
+# O(N^2) amplification of the derivative and lift operators on rough data.
+# Measured: 1.3e-7 (48^3, N=7, sampled elements), 8.5e-8 (smoke); the bound is
+# about ten times that.  The tensor-core FP16 form (hi/lo split of 11-bit
+# halves with a power-of-two scale per line group: about 22 bits per operand,
+# products exact, FP32 sums) is held to the same bound.
+MIXED_RHS_TOL = 1e-6
+# BF16 hi/lo keeps 16 of FP32's 24 mantissa bits per operand: the dropped
+# lo*lo product and the rounding of lo leave about 2^-17 relative per term.
+BF16_RHS_TOL = 5e-5
+TC_TOL = {"mixed": MIXED_RHS_TOL, "mixed_tc": MIXED_RHS_TOL, "mixed_tc_bf16": BF16_RHS_TOL}
+# Ten LSRK steps of the parity workload (50 stages) against the oracle.
+STEP10_TOL = {"mixed": 1e-6, "mixed_tc": 1e-6, "mixed_tc_bf16": 2e-5}
+
 
 def rel_l2(a, b):
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def elem_max_rel(a, b):
+    """Largest per-element error: max over elements e of max |a_e - b_e| (all
+    fields and nodes of e), relative to max |b| over the whole array.  Arrays
+    are [m][nel][Np] (or a sample of elements on the middle axis).  One wrong
+    node shows here at its own size, where a global L2 norm dilutes it."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.abs(a - b).max(axis=(0, 2)).max() / np.abs(b).max())
+
+
+def assert_parity(got, want, tol, tol_elem=None, label=""):
+    """Global relative L2 <= tol and per-element maximum error <= tol_elem
+    (default: tol); returns both measures."""
+    e2, em = rel_l2(got, want), elem_max_rel(got, want)
+    te = tol if tol_elem is None else tol_elem
+    if label:
+        print(f"{label}: rel L2 {e2:.3e}, element max {em:.3e}")
+    assert e2 < tol and em < te, f"{label} rel L2 {e2:.3e} (bound {tol:.1e}), element max {em:.3e} (bound {te:.1e})"
+    return e2, em
 
 
 class Case:

@@ -121,3 +121,22 @@ def test_every_declaration_is_documented():
     # calls documented together with the call right above them
     grouped = {"dgw_destroy", "dgw_batch_destroy", "dgw_batch_last_error", "dgw_abi_version"}
     assert not [f for f in undocumented if f not in grouped], undocumented
+
+
+def test_energy_static_refuses_host_arrays(lib):
+    """dgw_energy_static takes only device memory of the current device: plain
+    host arrays are refused with DGW_ERR_ARG before anything is launched (no
+    GPU needed to see it)."""
+    from paper_1711_01175_gb300 import capi
+    host = np.zeros(64 * 27)
+    p = host.ctypes.data
+    assert capi.dgw_energy_static(2, 1, p, p, p, p, p, p, None) == -1
+    assert "device memory" in capi.dgw_last_error(None)
+
+
+def test_create_refuses_unknown_precision(lib):
+    from paper_1711_01175_gb300 import capi
+    for prec in (-1, 4):
+        cfg = capi.dgw_config(3, 1, prec, 0.5, 0, (ctypes.c_double * 3)(0, 0, 0))
+        st, _ = capi.dgw_create(0, cfg)
+        assert st == -1 and "precision" in capi.dgw_last_error(None)

@@ -14,7 +14,7 @@ import pytest
 
 import oracle
 import workloads as wl
-from harness import rel_l2
+from harness import assert_parity, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -97,10 +97,10 @@ def test_batch_matches_single_solves_with_composition_change(precision):
     b.run(2, stream)
     torch.cuda.synchronize()
     tol = BATCH_TOL[precision]
-    assert rel_l2(got_left, alone(left, 4)) < tol
-    assert rel_l2(items[0]["u"].cpu().numpy(), alone(items[0], 8)) < tol
-    assert rel_l2(items[2]["u"].cpu().numpy(), alone(items[2], 8)) < tol
-    assert rel_l2(late["u"].cpu().numpy(), alone(late, 4)) < tol
+    assert_parity(got_left, alone(left, 4), tol)
+    assert_parity(items[0]["u"].cpu().numpy(), alone(items[0], 8), tol)
+    assert_parity(items[2]["u"].cpu().numpy(), alone(items[2], 8), tol)
+    assert_parity(late["u"].cpu().numpy(), alone(late, 4), tol)
     b.close()
 
 
@@ -123,7 +123,7 @@ def test_batched_solve_matches_oracle():
     uo, ro = it["u0"].copy(), np.zeros_like(it["u0"])
     for k in range(2):
         uo, ro = op.step(uo, ro, it["dt"], t=k * it["dt"])
-    assert rel_l2(it["u"].cpu().numpy(), uo) < 1e-12
+    assert_parity(it["u"].cpu().numpy(), uo, 1e-12)
     b.close()
 
 

@@ -16,7 +16,7 @@ import pytest
 
 import oracle
 import workloads as wl
-from harness import rel_l2
+from harness import assert_parity, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -71,7 +71,7 @@ def test_rhs_parity(system, N, E, tau):
     u = _dev(c.u0)
     out = torch.empty_like(u)
     c.solver.rhs(u, out)
-    assert rel_l2(out.cpu().numpy(), c.op.rhs(c.u0)) < TOL
+    assert_parity(out.cpu().numpy(), c.op.rhs(c.u0), TOL)
 
 
 @pytest.mark.parametrize("system,E", [("transport", 3), ("shallow_water", (4, 3, 1))])
@@ -95,8 +95,8 @@ def test_stages_step_and_energy_parity(system, E):
                                                 s, 0.0, dt, stream)
             assert st == 0
         uo, ro = c.op.lsrk_stage(uo, ro, s, dt)
-        assert rel_l2(u_out.cpu().numpy(), uo) < TOL
-        assert rel_l2(res.cpu().numpy(), ro) < TOL
+        assert_parity(u_out.cpu().numpy(), uo, TOL)
+        assert_parity(res.cpu().numpy(), ro, TOL)
         u_in, u_out = u_out, u_in
     E_ref = c.op.energy(uo)
     assert abs(e_fused - E_ref) <= TOL * E_ref
@@ -108,7 +108,7 @@ def test_stages_step_and_energy_parity(system, E):
     u2, r2 = c.u0.copy(), np.zeros_like(c.u0)
     for k in range(2):
         u2, r2 = c.op.step(u2, r2, dt, t=k * dt)
-    assert rel_l2(u.cpu().numpy(), u2) < TOL
+    assert_parity(u.cpu().numpy(), u2, TOL)
 
 
 def test_standing_wave_converges_at_design_order_on_the_gpu():

@@ -19,7 +19,7 @@ import pytest
 
 import oracle
 import workloads as wl
-from harness import rel_l2
+from harness import assert_parity, rel_l2
 from oracle.ihdg import IHDGTransport
 
 pytestmark = pytest.mark.gpu
@@ -76,7 +76,7 @@ def test_iterates_match_the_oracle(N):
         u = torch.zeros_like(fd)
         its, _ = s.ihdg_solve(u, f=fd, tol=0.0, max_iter=k)
         assert its == k
-        assert rel_l2(u.cpu().numpy(), iterates[k]) < 1e-11, k
+        assert_parity(u.cpu().numpy(), iterates[k], 1e-11)
 
 
 def test_converged_solution_is_the_direct_solution():
@@ -88,7 +88,7 @@ def test_converged_solution_is_the_direct_solution():
     its, change = s.ihdg_solve(u, f=_dev(f), tol=1e-10)
     assert its == 3 * 3 - 1 and change < 1e-10
     ud = IHDGTransport(op, 0.0).direct(f)
-    assert rel_l2(u.cpu().numpy(), ud) < 1e-10
+    assert_parity(u.cpu().numpy(), ud, 1e-10)
 
 
 def _golden():
@@ -153,7 +153,7 @@ def test_locally_implicit_step_is_the_implicit_euler_step():
     its, change = s.ihdg_solve(u, u_prev=_dev(um), tol=1e-12, max_iter=200)
     assert change < 1e-12 and its < 60
     ud = IHDGTransport(op, 1.0 / dt).direct(um / dt)
-    assert rel_l2(u.cpu().numpy(), ud) < 1e-10
+    assert_parity(u.cpu().numpy(), ud, 1e-10)
 
 
 def test_refusals():
@@ -219,7 +219,7 @@ def test_shallow_water_iterates_match_the_oracle(N):
         u = umd.clone()
         its, _ = s.ihdg_solve(u, u_prev=umd, f=f, tol=0.0, max_iter=k)
         assert its == k
-        assert rel_l2(u.cpu().numpy(), iterates[k]) < 1e-11, k
+        assert_parity(u.cpu().numpy(), iterates[k], 1e-11)
 
 
 def _sw_golden():
@@ -291,7 +291,7 @@ def test_elastic_iterates_match_the_oracle(N, E):
         u = u0d.clone()
         its, _ = s.ihdg_solve(u, u_prev=u0d, tol=0.0, max_iter=k)
         assert its == k
-        assert rel_l2(u.cpu().numpy(), iterates[k]) < 1e-11, k
+        assert_parity(u.cpu().numpy(), iterates[k], 1e-11)
 
 
 def test_elastic_converged_step_is_the_direct_implicit_step():
@@ -307,7 +307,7 @@ def test_elastic_converged_step_is_the_direct_implicit_step():
     u = u0d.clone()
     its, change = s.ihdg_solve(u, u_prev=u0d, tol=1e-10, max_iter=500)
     assert abs(its - its_or) <= 1 and change < 1e-10
-    assert rel_l2(u.cpu().numpy(), ud) < 1e-9
+    assert_parity(u.cpu().numpy(), ud, 1e-9)
 
 
 @pytest.mark.parametrize("scheme", ["euler", "crank_nicolson"])

@@ -8,14 +8,11 @@ import pytest
 
 import oracle
 import workloads as wl
-from harness import Case, rel_l2
+from harness import (BF16_RHS_TOL, FP64_TOL, MIXED_RHS_TOL, STEP10_TOL, TC_TOL, Case, assert_parity,
+                     elem_max_rel, rel_l2)
 
 pytestmark = pytest.mark.gpu
 
-FP64_TOL = 1e-12
-# FP32 volume/flux arithmetic on FP32 geometry: unit round-off 6e-8 times the
-# O(N^2) amplification of the derivative and lift operators on rough data.
-MIXED_RHS_TOL = 2e-5
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -33,7 +30,7 @@ def torch_cuda(a):
 def test_rhs_parity_workload_plane_wave():
     cfg = wl.parity_config()
     c = Case(cfg.E, cfg.N, cfg.amplitude, cfg.periodic, initial="plane_p_wave")
-    assert rel_l2(c.gpu_rhs(c.u0), c.op.rhs(c.u0)) < FP64_TOL
+    assert_parity(c.gpu_rhs(c.u0), c.op.rhs(c.u0), FP64_TOL)
 
 
 @pytest.mark.parametrize("N", range(1, 8))
@@ -43,18 +40,18 @@ def test_rhs_parity_every_degree_rotated_ragged(N):
     c = Case(3, N, 0.08, periodic=(True, False, False),
              boundary={2: wl.BC_FREE_SURFACE, 3: wl.BC_ABSORBING, 4: wl.BC_ABSORBING, 5: wl.BC_FREE_SURFACE},
              material=N, rotate=100 + N, seed=N)
-    assert rel_l2(c.gpu_rhs(c.u0), c.op.rhs(c.u0)) < FP64_TOL
+    assert_parity(c.gpu_rhs(c.u0), c.op.rhs(c.u0), FP64_TOL)
 
 
 def test_rhs_parity_single_self_periodic_element():
     c = Case(1, 4, 0.08, seed=3)
-    assert rel_l2(c.gpu_rhs(c.u0), c.op.rhs(c.u0)) < FP64_TOL
+    assert_parity(c.gpu_rhs(c.u0), c.op.rhs(c.u0), FP64_TOL)
 
 
 @pytest.mark.parametrize("tau", [0, 1])
 def test_rhs_parity_flux_choice(tau):
     c = Case(3, 3, 0.1, material=7, tau=tau, seed=4)
-    assert rel_l2(c.gpu_rhs(c.u0), c.op.rhs(c.u0)) < FP64_TOL
+    assert_parity(c.gpu_rhs(c.u0), c.op.rhs(c.u0), FP64_TOL)
 
 
 def test_rhs_parity_large_cut():
@@ -63,9 +60,9 @@ def test_rhs_parity_large_cut():
     cfg = wl.large_config(E=16)
     c = Case(cfg.E, cfg.N, cfg.amplitude, cfg.periodic, cfg.boundary, cfg.order, material=1,
              initial="gaussian_pulse")
-    assert rel_l2(c.gpu_rhs(c.u0), c.op.rhs(c.u0)) < FP64_TOL
+    assert_parity(c.gpu_rhs(c.u0), c.op.rhs(c.u0), FP64_TOL)
     u = wl.random_state(c.mesh.nel, 125, 9)
-    assert rel_l2(c.gpu_rhs(u), c.op.rhs(u)) < FP64_TOL
+    assert_parity(c.gpu_rhs(u), c.op.rhs(u), FP64_TOL)
 
 
 # ---------------------------------------------------------------- stage parity
@@ -80,7 +77,8 @@ def _stages(c, dt):
     for s in range(5):
         c.solver.stage(u, u_next, res, s, dt)
         uo, ro = c.op.lsrk_stage(uo, ro, s, dt)
-        worst = max(worst, rel_l2(u_next.cpu().numpy(), uo), rel_l2(res.cpu().numpy(), ro))
+        un, rn = u_next.cpu().numpy(), res.cpu().numpy()
+        worst = max(worst, rel_l2(un, uo), rel_l2(rn, ro), elem_max_rel(un, uo), elem_max_rel(rn, ro))
         u, u_next = u_next, u
     return worst
 
@@ -113,8 +111,8 @@ def test_parity_workload_100_steps():
     uo, ro = c.u0.copy(), np.zeros_like(c.u0)
     for _ in range(cfg.steps):
         uo, ro = c.op.step(uo, ro, dt)
-    assert rel_l2(u.cpu().numpy(), uo) < FP64_TOL
-    assert rel_l2(res.cpu().numpy(), ro) < 1e-11
+    assert_parity(u.cpu().numpy(), uo, FP64_TOL)
+    assert_parity(res.cpu().numpy(), ro, 1e-11)
 
 
 def test_point_source_parity_rhs_and_step():
@@ -130,19 +128,19 @@ def test_point_source_parity_rhs_and_step():
     ud = torch_cuda(u0)
     out = torch.empty_like(ud)
     c.solver.rhs(ud, out, t=0.13)
-    assert rel_l2(out.cpu().numpy(), c.op.rhs(u0, t=0.13)) < FP64_TOL
+    assert_parity(out.cpu().numpy(), c.op.rhs(u0, t=0.13), FP64_TOL)
     dt = c.solver.dt_cfl()
     res = torch.zeros_like(ud)
     c.solver.step(ud, res, dt, 2, t0=0.08)
     uo, ro = u0.copy(), np.zeros_like(u0)
     for k in range(2):
         uo, ro = c.op.step(uo, ro, dt, t=0.08 + k * dt)
-    assert rel_l2(ud.cpu().numpy(), uo) < FP64_TOL
+    assert_parity(ud.cpu().numpy(), uo, FP64_TOL)
     # removing the source restores the source-free operator
     c.solver.set_point_force(-1, [0, 0, 0], [0, 0, 0], 1.0, 0.0)
     c.op.source = None
     c.solver.rhs(torch_cuda(u0), out, t=0.13)
-    assert rel_l2(out.cpu().numpy(), c.op.rhs(u0, t=0.13)) < FP64_TOL
+    assert_parity(out.cpu().numpy(), c.op.rhs(u0, t=0.13), FP64_TOL)
 
 
 # ---------------------------------------------------------------------- energy
@@ -208,19 +206,48 @@ def test_host_pointer_paths_match_device_paths():
 
 
 # -------------------------------------------------------------- mixed precision
-def test_mixed_precision_rhs_bound():
+@pytest.mark.parametrize("precision", ["mixed", "mixed_tc", "mixed_tc_bf16"])
+def test_mixed_precision_rhs_bound(precision):
     cfg = wl.large_config(E=8)
     for initial in ("gaussian_pulse", "random"):
         c = Case(cfg.E, cfg.N, cfg.amplitude, cfg.periodic, cfg.boundary, cfg.order, material=1,
-                 initial=initial, precision="mixed")
-        err = rel_l2(c.gpu_rhs(c.u0), c.op.rhs(c.u0))
-        assert err < MIXED_RHS_TOL, err
+                 initial=initial, precision=precision)
+        assert_parity(c.gpu_rhs(c.u0), c.op.rhs(c.u0), TC_TOL[precision], label=f"{precision} 8^3 {initial}")
 
 
-def test_mixed_precision_step_bound():
+@pytest.mark.parametrize("precision", ["mixed_tc", "mixed_tc_bf16"])
+@pytest.mark.parametrize("N", range(1, 8))
+def test_tensor_core_rhs_every_degree_rotated_ragged(N, precision):
+    """The tensor-core volume form at every degree: 27 rotated elements (all
+    eight face permutations, ragged last CTA for N <= 3), free-surface and
+    absorbing faces, heterogeneous medium, random state."""
+    c = Case(3, N, 0.08, periodic=(True, False, False),
+             boundary={2: wl.BC_FREE_SURFACE, 3: wl.BC_ABSORBING, 4: wl.BC_ABSORBING, 5: wl.BC_FREE_SURFACE},
+             material=N, rotate=100 + N, seed=N, precision=precision)
+    assert_parity(c.gpu_rhs(c.u0), c.op.rhs(c.u0), TC_TOL[precision], label=f"{precision} N={N}")
+
+
+@pytest.mark.parametrize("precision", ["mixed_tc", "mixed_tc_bf16"])
+def test_tensor_core_rhs_scale_invariance(precision):
+    """Stresses 1e6 times the velocities (a medium in SI-like units): the FP16
+    form's per-row power-of-two scaling keeps the same relative accuracy, and
+    the state's own scale does not enter either form."""
+    c = Case(3, 4, 0.1, material=2, seed=11, precision=precision)
+    u = c.u0.copy()
+    u[3:] *= 1e6
+    want = c.op.rhs(u)
+    assert_parity(c.gpu_rhs(u), want, TC_TOL[precision], label=f"{precision} stress x 1e6")
+    assert_parity(c.gpu_rhs(1e-30 * u), 1e-30 * want, TC_TOL[precision], label=f"{precision} state x 1e-30")
+
+
+@pytest.mark.parametrize("precision", ["mixed", "mixed_tc", "mixed_tc_bf16"])
+def test_mixed_precision_step_bound(precision):
+    """Ten LSRK steps of the parity workload (4^3, N=3, plane wave, CFL 0.5)
+    against the FP64 oracle: the FP32 right-hand side error (~1e-7 per stage)
+    accumulates over 50 stages with dt ~ 7e-3."""
     import torch
     cfg = wl.parity_config()
-    c = Case(cfg.E, cfg.N, cfg.amplitude, cfg.periodic, initial="plane_p_wave", precision="mixed")
+    c = Case(cfg.E, cfg.N, cfg.amplitude, cfg.periodic, initial="plane_p_wave", precision=precision)
     dt = c.solver.dt_cfl()
     u = torch_cuda(c.u0)
     res = torch.zeros_like(u)
@@ -228,7 +255,31 @@ def test_mixed_precision_step_bound():
     uo, ro = c.u0.copy(), np.zeros_like(c.u0)
     for _ in range(10):
         uo, ro = c.op.step(uo, ro, dt)
-    assert rel_l2(u.cpu().numpy(), uo) < 1e-6
+    assert_parity(u.cpu().numpy(), uo, STEP10_TOL[precision], label=f"{precision} 10 steps")
+
+
+@pytest.mark.parametrize("precision", ["mixed_tc", "mixed_tc_bf16"])
+def test_tensor_core_stage_and_fused_energy(precision):
+    """The tensor-core form through the fused LSRK stage (register update in FP64)
+    and the fused-energy stage, on a 6^3 cut of the large workload: stage output
+    against the oracle's stage, and the fused energy against dgw_energy."""
+    import torch
+    cfg = wl.large_config(E=6)
+    c = Case(cfg.E, cfg.N, cfg.amplitude, cfg.periodic, cfg.boundary, cfg.order, material=1,
+             initial="gaussian_pulse", precision=precision)
+    dt = c.solver.dt_cfl()
+    u = torch_cuda(c.u0)
+    res0 = torch_cuda(wl.random_state(c.mesh.nel, 125, 5)) * 1e-3
+    out_a, out_b = torch.empty_like(u), torch.empty_like(u)
+    res_a, res_b = res0.clone(), res0.clone()
+    c.solver.stage(u, out_a, res_a, 2, dt)
+    e = c.solver.stage_energy(u, out_b, res_b, 2, dt)
+    assert torch.equal(out_a, out_b) and torch.equal(res_a, res_b)
+    assert abs(e - c.solver.energy(out_b)) <= 1e-13 * e
+    uo, ro = c.op.lsrk_stage(c.u0, res0.cpu().numpy(), 2, dt)
+    # the stage changes u by b_s res ~ dt L(u): compare the increments
+    assert_parity(out_a.cpu().numpy() - c.u0, uo - c.u0, TC_TOL[precision], label=f"{precision} stage increment")
+    assert_parity(res_a.cpu().numpy(), ro, TC_TOL[precision], label=f"{precision} stage register")
 
 
 # ------------------------------------------------------------------ full size
@@ -250,7 +301,7 @@ def test_full_size_large_workload_sampled():
     u = wl.random_state(nel, 125, 21)
     got = c.gpu_rhs(u)[:, sample]
     want = c.op.rhs(u, sample)
-    assert rel_l2(got, want) < FP64_TOL
+    assert_parity(got, want, FP64_TOL)
     # first LSRK stage from the Gaussian pulse
     ud = torch_cuda(c.u0)
     uo_d = torch.empty_like(ud)
@@ -258,8 +309,8 @@ def test_full_size_large_workload_sampled():
     dt = c.solver.dt_cfl()
     c.solver.stage(ud, uo_d, res, 0, dt)
     u1, r1 = c.op.lsrk_stage(c.u0, np.zeros_like(c.u0), 0, dt, sample)
-    assert rel_l2(uo_d.cpu().numpy()[:, sample], u1) < FP64_TOL
-    assert rel_l2(res.cpu().numpy()[:, sample], r1) < FP64_TOL
+    assert_parity(uo_d.cpu().numpy()[:, sample], u1, FP64_TOL)
+    assert_parity(res.cpu().numpy()[:, sample], r1, FP64_TOL)
 
 
 def test_full_size_precision_workload_sampled():
@@ -280,19 +331,16 @@ def test_full_size_precision_workload_sampled():
                                        rng.choice(top, 6), [0, nel - 1]]))
     u = wl.random_state(nel, Np, 22)
     want = c.op.rhs(u, sample)
-    err64 = rel_l2(c.gpu_rhs(u)[:, sample], want)
-    print(f"48^3 N=7 sampled: FP64 rel L2 {err64:.3e}")
-    assert err64 < FP64_TOL, err64
-    m = Solver(cfg.N, precision="mixed")
-    m.upload_mesh(c.x_lib, c.mesh.etoe, c.mesh.etof, c.mesh.orient, c.mesh.bc)
-    m.upload_material(c.rho, c.lam, c.mu)
+    assert_parity(c.gpu_rhs(u)[:, sample], want, FP64_TOL, label="48^3 N=7 sampled FP64")
     ud = torch.from_numpy(u).cuda()
     out = torch.empty_like(ud)
-    m.rhs(ud, out)
-    err = rel_l2(out.cpu().numpy()[:, sample], want)
-    print(f"48^3 N=7 sampled: mixed rel L2 {err:.3e}")
-    assert err < MIXED_RHS_TOL, err
-    m.close()
+    for prec in ("mixed", "mixed_tc", "mixed_tc_bf16"):
+        m = Solver(cfg.N, precision=prec)
+        m.upload_mesh(c.x_lib, c.mesh.etoe, c.mesh.etof, c.mesh.orient, c.mesh.bc)
+        m.upload_material(c.rho, c.lam, c.mu)
+        m.rhs(ud, out)
+        assert_parity(out.cpu().numpy()[:, sample], want, TC_TOL[prec], label=f"48^3 N=7 sampled {prec}")
+        m.close()
 
 
 # -------------------------------------------------------------- argument errors

@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 import workloads as wl
-from harness import rel_l2
+from harness import assert_parity, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -44,7 +44,7 @@ def test_each_result_same_alone_and_in_the_mix(precision, tol, ticks):
     for rid in mixed:
         a, b = mixed[rid]["state"], alone[rid]["state"]
         assert np.linalg.norm(b) > 0
-        assert rel_l2(a, b) < tol, (rid, rel_l2(a, b))
+        assert_parity(a, b, tol)
         assert abs(mixed[rid]["energy"] - alone[rid]["energy"]) <= 1e3 * tol * alone[rid]["energy"]
     s = serving.summarize(mixed, wall)
     assert s["p99_ms"] >= s["p50_ms"] > 0
@@ -57,4 +57,4 @@ def test_memory_budget_admits_as_memory_frees():
     res, _ = serving.continuous_batching(reqs, precision="fp64", memory_budget=biggest * 1.5, keep_states=True)
     alone, _ = serving.one_at_a_time(reqs, precision="fp64", keep_states=True)
     for rid in res:
-        assert rel_l2(res[rid]["state"], alone[rid]["state"]) < 1e-12
+        assert_parity(res[rid]["state"], alone[rid]["state"], 1e-12)
