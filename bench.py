@@ -317,6 +317,45 @@ def run_ab_precision(args, device, stream, hbm_peak, peak_kind):
     return out
 
 
+def run_precision_recipe(T, device):
+    """The precision recipe at full size (48^3, N=7): FP64, the FP32 CUDA-core
+    mixed form and the tensor-core FP16 hi/lo mixed form advanced from the
+    Gaussian pulse to time T with the same steps (dt = T / ceil(T / dt_cfl));
+    the FP64 state is the reference (the parity tests hold it to the oracle at
+    1e-12 per stage).  Relative L2 error of each mixed state at T, the energy
+    drift |E_mixed(T) - E_fp64(T)| / E(0), and the wall time of each run."""
+    import math
+    import torch
+    cfg, data = build_workload("precision")
+    out = {"workload": workload_name(cfg), "T": T}
+    states, energies = {}, {}
+    for prec in ("fp64", "mixed", "mixed_tc"):
+        s = setup_solver(prec, cfg, data)
+        if prec == "fp64":
+            nsteps = math.ceil(T / s.dt_cfl())
+            dt = T / nsteps
+            out.update(steps=nsteps, dt=dt)
+        u = torch.from_numpy(data["u0"]).to(device)
+        res = torch.zeros_like(u)
+        e0 = s.energy(u)
+        torch.cuda.synchronize(device)
+        t0 = time.perf_counter()
+        s.step(u, res, dt, nsteps)
+        torch.cuda.synchronize(device)
+        wall = time.perf_counter() - t0
+        energies[prec] = (e0, s.energy(u))
+        states[prec] = u.cpu().numpy()
+        out[prec] = {"wall_s": wall, "E_T_over_E0": energies[prec][1] / e0}
+        s.close()
+        del u, res
+        torch.cuda.empty_cache()
+    ref = states["fp64"]
+    for prec in ("mixed", "mixed_tc"):
+        out[prec]["rel_l2_vs_fp64"] = float(np.linalg.norm(states[prec] - ref) / np.linalg.norm(ref))
+        out[prec]["energy_drift"] = abs(energies[prec][1] - energies["fp64"][1]) / energies["fp64"][0]
+    return out
+
+
 def run_e2e(precision, cfg, data, steps, warmup, device, stream):
     """Through the public call with a pinned host state: dgw_step_energy(host u,
     res = NULL, 1 step) copies u in, runs the five stages (the last one also
@@ -420,32 +459,53 @@ def reference_arm(args):
 
 
 def run_serving(args):
-    """Served latency: the same seeded request stream through continuous batching
-    and through one-at-a-time plain solves (mixed path).  Request payloads (mesh,
-    medium, point force) are prepared before the clock starts, as a client would
-    send them."""
+    """Served latency: one seeded request stream through continuous batching and
+    through one-at-a-time plain solves (mixed path), at each arrival rate of
+    --serve-rates (Poisson arrivals; the same requests at every rate, arrival
+    times scaled).  Request payloads (mesh, medium, point force) are prepared
+    before the clock starts, as a client would send them.  The device's
+    capacity for the stream is estimated from the one-at-a-time run at the
+    highest rate (busy the whole time): rates below it measure batching
+    latency, rates above it measure queueing."""
     from paper_1711_01175_gb300 import serving, reference_nodes
-    reqs = wl.make_requests(args.serve_requests, seed=7, rate=args.serve_rate,
-                            E_range=(8, args.serve_max_E), N_choices=(3, 4, 5),
+    rates = [float(v) for v in str(args.serve_rates).split(",") if v.strip()]
+    base = wl.make_requests(args.serve_requests, seed=7, rate=1.0, E_range=(8, args.serve_max_E), N_choices=(3, 4, 5),
                             steps_range=(args.serve_min_steps, args.serve_max_steps))
-    for r in reqs:
+    t_build = time.perf_counter()
+    for r in base:
         r.payload = r.build(reference_nodes(r.N)[0])
+    t_build = time.perf_counter() - t_build
     warm = wl.make_requests(3, seed=8, rate=1000.0, E_range=(2, 3), N_choices=(3, 4, 5), steps_range=(2, 4))
     for r in warm:
         r.payload = r.build(reference_nodes(r.N)[0])
     serving.continuous_batching(warm, precision="mixed")
     serving.one_at_a_time(warm, precision="mixed")
-    res_b, wall_b = serving.continuous_batching(reqs, precision="mixed", memory_budget=args.serve_memory_gb * 1e9)
-    res_s, wall_s = serving.one_at_a_time(reqs, precision="mixed")
-    dof_stages = sum(r.E ** 3 * (r.N + 1) ** 3 * 9 * 5 * r.steps for r in reqs)
-    b, s1 = serving.summarize(res_b, wall_b), serving.summarize(res_s, wall_s)
-    b["dof_stage_updates_per_s"] = dof_stages / wall_b
-    s1["dof_stage_updates_per_s"] = dof_stages / wall_s
-    return {"requests": len(reqs), "rate_per_s": args.serve_rate, "mesh_E": [8, args.serve_max_E], "N": [3, 4, 5],
+    dof_stages = sum(r.E ** 3 * (r.N + 1) ** 3 * 9 * 5 * r.steps for r in base)
+    sweep = []
+    for rate in rates:
+        arrivals = [r.arrival for r in base]
+        for r, a in zip(base, arrivals):
+            r.arrival = a / rate
+        res_b, wall_b = serving.continuous_batching(base, precision="mixed", memory_budget=args.serve_memory_gb * 1e9)
+        res_s, wall_s = serving.one_at_a_time(base, precision="mixed")
+        for r, a in zip(base, arrivals):
+            r.arrival = a
+        b, s1 = serving.summarize(res_b, wall_b), serving.summarize(res_s, wall_s)
+        b["dof_stage_updates_per_s"] = dof_stages / wall_b
+        s1["dof_stage_updates_per_s"] = dof_stages / wall_s
+        sweep.append({"rate_per_s": rate, "continuous_batching": b, "one_at_a_time": s1})
+    busiest = max(sweep, key=lambda x: x["rate_per_s"])
+    capacity = busiest["one_at_a_time"]["solves_per_s"]
+    for x in sweep:
+        x["load_vs_one_at_a_time_capacity"] = x["rate_per_s"] / capacity
+    below = [x for x in sweep if x["rate_per_s"] < capacity]
+    head = min(below, key=lambda x: x["rate_per_s"]) if below else min(sweep, key=lambda x: x["rate_per_s"])
+    return {"requests": len(base), "mesh_E": [8, args.serve_max_E], "N": [3, 4, 5],
             "steps": [args.serve_min_steps, args.serve_max_steps], "precision": "mixed",
-            "memory_budget_gb": args.serve_memory_gb,
-            "continuous_batching": b, "one_at_a_time": s1,
-            "p99_ms": b["p99_ms"], "p50_ms": b["p50_ms"]}
+            "memory_budget_gb": args.serve_memory_gb, "payload_build_s": t_build,
+            "one_at_a_time_capacity_solves_per_s": capacity, "rates": sweep,
+            "p99_ms": head["continuous_batching"]["p99_ms"], "p50_ms": head["continuous_batching"]["p50_ms"],
+            "headline_rate_per_s": head["rate_per_s"]}
 
 
 def run_adjoint(args):
@@ -454,9 +514,10 @@ def run_adjoint(args):
     sweep; reports the time of each and their ratio.  The experiment: a Ricker
     point force at the centre element (peak frequency 3 / window, centred at
     1.2 / f0 so that it starts from rest), receivers at random points of the
-    source element and its face neighbours (what the window's waves reach at
-    CFL 0.5), data recorded in the same experiment with the medium perturbed
-    by 5 % seeded noise (untimed), L2 misfit."""
+    elements within two faces of the source element (what the window's waves
+    reach at CFL 0.5), data recorded in the same experiment with the medium
+    perturbed by 5 % seeded noise (untimed), L2 misfit.  Defaults: the adjoint
+    recipe (32^3, N=4, 500 steps, 32 receivers, checkpoints every 50)."""
     import torch
     from paper_1711_01175_gb300 import Solver, reference_nodes
     from paper_1711_01175_gb300.adjoint import receiver_traces
@@ -474,7 +535,9 @@ def run_adjoint(args):
     s.set_point_force(centre, [0.1, -0.2, 0.3], [0.0, 0.0, 1.0], f0, 1.2 / f0)
     rng = np.random.default_rng(9)
     near = [centre] + [int(e) for e in mesh.etoe[centre] if e >= 0]
-    s.set_receivers(rng.choice(near, nrec), rng.uniform(-0.9, 0.9, (nrec, 3)))
+    around = np.unique(np.concatenate([mesh.etoe[e] for e in near]))
+    around = around[around >= 0]              # within two faces of the source
+    s.set_receivers(rng.choice(around, nrec), rng.uniform(-0.9, 0.9, (nrec, 3)))
     u0 = torch.zeros((9, mesh.nel, (N + 1) ** 3), dtype=torch.float64, device="cuda")
     base = np.stack([rho, lam, mu])
     perturbed = base * (1.0 + 0.05 * rng.uniform(-1.0, 1.0, base.shape))
@@ -503,6 +566,7 @@ def run_adjoint(args):
             "misfit": float(J.detach()), "trace_rms": float(torch.sqrt(torch.mean(tr.detach() ** 2))),
             "gradient_norm": float(np.linalg.norm(g)),
             "gradient_share_source_and_neighbours": float(g2[:, near].sum() / g2.sum()),
+            "gradient_share_within_two_faces": float(g2[:, around].sum() / g2.sum()),
             "precision": "fp64"}
 
 
@@ -770,18 +834,27 @@ def main():
     ap.add_argument("--ihdg-elastic-E", type=int, default=16,
                     help="elastic iHDG-II mesh edge (N = 2; 0 skips the elastic part)")
     ap.add_argument("--fr-steps", type=int, default=20)
-    ap.add_argument("--adj-E", type=int, default=16, help="adjoint mesh edge (the full recipe: 32)")
-    ap.add_argument("--adj-steps", type=int, default=40, help="(the full recipe: 500)")
-    ap.add_argument("--adj-receivers", type=int, default=8, help="(the full recipe: 32)")
-    ap.add_argument("--adj-checkpoint", type=int, default=10, help="(the full recipe: 50)")
+    ap.add_argument("--adj-E", type=int, default=32, help="adjoint mesh edge (the recipe: 32)")
+    ap.add_argument("--adj-steps", type=int, default=500, help="(the recipe: 500)")
+    ap.add_argument("--adj-receivers", type=int, default=32, help="(the recipe: 32)")
+    ap.add_argument("--adj-checkpoint", type=int, default=50, help="(the recipe: 50)")
     ap.add_argument("--serve-requests", type=int, default=160,
                     help="requests of the served-latency run (the full recipe: 2000)")
-    ap.add_argument("--serve-rate", type=float, default=80.0, help="Poisson arrival rate per second")
+    ap.add_argument("--serve-rates", default="20,40,80",
+                    help="Poisson arrival rates per second, comma separated (the full recipe: about 0.7 solves/s of capacity)")
+    ap.add_argument("--serve-recipe", action="store_true",
+                    help="the serving recipe's distributions: meshes 8^3..48^3, 200-2000 steps (with --serve-requests, "
+                         "--serve-rates)")
+    ap.add_argument("--serving-only", action="store_true", help="print a line with the serving section only")
+    ap.add_argument("--precision-recipe-T", type=float, default=None,
+                    help="print a line with the precision recipe (48^3, N=7) advanced to this time only")
     ap.add_argument("--serve-max-E", type=int, default=20, help="largest mesh edge (the full recipe: 48)")
     ap.add_argument("--serve-min-steps", type=int, default=40, help="(the full recipe: 200)")
     ap.add_argument("--serve-max-steps", type=int, default=120, help="(the full recipe: 2000)")
     ap.add_argument("--serve-memory-gb", type=float, default=40.0, help="device memory the server may hold")
     args = ap.parse_args()
+    if args.serve_recipe:
+        args.serve_max_E, args.serve_min_steps, args.serve_max_steps = 48, 200, 2000
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":
@@ -806,6 +879,16 @@ def main():
         torch.distributed.barrier()
     g.build()
 
+    if args.precision_recipe_T is not None:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "unit": UNIT, "data": "synthetic (seeded medium, Gaussian pulse)",
+                              "precision_recipe": run_precision_recipe(args.precision_recipe_T, device)}), flush=True)
+        return
+    if args.serving_only:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "unit": UNIT, "data": "synthetic (seeded request stream)",
+                              "serving": run_serving(args)}), flush=True)
+        return
     cfg, data = build_workload(args.workload, args.elements)
     hbm_peak, peak_kind = peaks()
     variants = {"all": ["fp64", "mixed", "mixed_tc", "mixed_tc_bf16"], "both": ["fp64", "mixed"]}.get(

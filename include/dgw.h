@@ -88,7 +88,7 @@ typedef struct {
 } dgw_config;
 
 /* ABI version of this header (bumped on any signature change). */
-#define DGW_ABI_VERSION 9
+#define DGW_ABI_VERSION 10
 int dgw_abi_version(void);
 
 /* GLL nodes r[0..N] (ascending, r[0] = -1, r[N] = +1) and weights w[0..N]
@@ -213,11 +213,27 @@ dgw_status dgw_source_set(dgw_ctx* ctx, int64_t element, const double* xi, const
  * on Q^{-1}, on the face impedances of the stabilisation and on the point
  * force.  The transpose uses L^T = (M Q) L_rev (M Q)^{-1}, L_rev the operator
  * with A_k -> -A_k (the upwind stabilisation of eq. RiemannFluxBoth is
- * symmetric and unchanged).  Stage inputs are recomputed from u_ckpt.  Adjoint
- * sources between steps (dgw_receivers_adjoint) need nsteps = 1 per call.
+ * symmetric and unchanged).  Stage inputs are recomputed from u_ckpt (once,
+ * all of them kept: (3 + 5 nsteps) state-sized buffers of context scratch).
+ * Adjoint sources between steps need either nsteps = 1 per call with
+ * dgw_receivers_adjoint between calls, or dgw_adjoint_traces.
  * Elastic FP64 contexts only (DGW_ERR_UNSUPPORTED otherwise). */
 dgw_status dgw_adjoint_step(dgw_ctx* ctx, double* lam_u, double* lam_res, double* grad_mat, const double* u_ckpt,
                             double t0, double dt, int nsteps, void* stream);
+
+/* dgw_adjoint_step for a misfit of receiver traces: the adjoint of the nsteps
+ * steps from the checkpoint u_ckpt (the state at t0), where before the
+ * transpose of step k (k = nsteps-1 down to 0) lam_u += S^T g_traces[k], S the
+ * receiver sampling of dgw_receivers_sample applied to the state after step k.
+ * g_traces: device [nsteps][nrec][3], the misfit's derivative with respect to
+ * the traces.  One call covers a whole checkpoint segment: the forward states
+ * are recomputed once from u_ckpt, keeping every stage input, which takes
+ * (3 + 5 nsteps) state-sized device buffers of context scratch (released with
+ * the context); DGW_ERR_OOM if they do not fit (use shorter segments).  Both
+ * adjoint calls share that scratch and reach it through the same recompute.
+ * DGW_ERR_STATE without receivers; otherwise as dgw_adjoint_step. */
+dgw_status dgw_adjoint_traces(dgw_ctx* ctx, double* lam_u, double* lam_res, double* grad_mat, const double* u_ckpt,
+                              const double* g_traces, double t0, double dt, int nsteps, void* stream);
 
 /* Receivers: velocity sampled at reference points xi[n][3] of elements[n]
  * (host arrays) with the element's Lagrange basis.  n = 0 removes them.

@@ -4,9 +4,10 @@
 from u0 with the per-element medium material = [rho, lam, mu] ([3, nel]
 float64) and returns the velocity at the solver's receivers after each step,
 [nsteps, nrec, 3].  Its backward pass is the hand-written discrete adjoint of
-the library (dgw_adjoint_step, dgw_receivers_adjoint): the forward states are
-kept only every `checkpoint_every` steps and recomputed segment by segment,
-so memory holds one segment of step states.  The gradient is exact for the
+the library (dgw_adjoint_traces): the forward states are kept only every
+`checkpoint_every` steps, and each segment's stage inputs are recomputed once
+from its checkpoint inside the library, so device memory holds one segment of
+stage inputs (5 states per step).  The gradient is exact for the
 discrete scheme (agreement with finite differences of any misfit of the
 traces up to their truncation error).
 """
@@ -45,15 +46,10 @@ class _ReceiverTraces(torch.autograd.Function):
         grad = torch.zeros((3, solver.nel), dtype=torch.float64, device=any_ckpt.device)
         for s0 in sorted(ctx.checkpoints, reverse=True):
             s1 = min(s0 + every, nsteps)
-            u = ctx.checkpoints[s0].clone()
-            res = torch.zeros_like(u)
-            starts = []
-            for k in range(s0, s1):
-                starts.append(u.clone())
-                solver.step(u, res, dt, 1, t0=k * dt)
-            for k in reversed(range(s0, s1)):
-                solver.receivers_adjoint(lam_u, g[k])
-                solver.adjoint_step(lam_u, lam_r, grad, starts[k - s0], dt, 1, t0=k * dt)
+            # one call per segment: the library recomputes the segment's stage
+            # inputs from the checkpoint and injects the trace sources step by step
+            solver.adjoint_traces(lam_u, lam_r, grad, ctx.checkpoints[s0], g[s0:s1].contiguous(), dt, s1 - s0,
+                                  t0=s0 * dt)
         return grad.to(ctx.material_device), None, None, None, None, None
 
 

@@ -54,6 +54,7 @@ SIGNATURES = {
     "dgw_receivers_sample": (_I, [_P, _P, _P, _P]),
     "dgw_receivers_adjoint": (_I, [_P, _P, _P, _P]),
     "dgw_adjoint_step": (_I, [_P, _P, _P, _P, _P, _D, _D, _I, _P]),
+    "dgw_adjoint_traces": (_I, [_P, _P, _P, _P, _P, _P, _D, _D, _I, _P]),
     "dgw_dt_cfl": (_I, [_P, ctypes.POINTER(_D)]),
     "dgw_batch_create": (_I, [ctypes.POINTER(_P), _I, _I, _I, _I, _I]),
     "dgw_batch_destroy": (_I, [_P]),

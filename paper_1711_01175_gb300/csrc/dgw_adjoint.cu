@@ -7,9 +7,10 @@
 // and linear in A_k (split-form volume term, central flux) and a symmetric
 // part independent of the sign of A_k (the upwind stabilisation), so
 // L^T = (M Q) L_rev (M Q)^{-1} with L_rev the operator for -A_k.  One adjoint
-// stage is three launches: the weight preparation (w, z = (M Q)^{-1} w,
-// lr <- a_s w), the gradient terms dt w^T (dL/dm) u_{s-1} on the recomputed
-// stage input, and the ADJ-mode stage kernel on z that adds dt M Q L_rev z.
+// stage is two launches: the weight preparation (w, z = (M Q)^{-1} w,
+// lr <- a_s w), then one kernel that on each tile computes the gradient terms
+// dt w^T (dL/dm) u_{s-1} on the recomputed stage input (GRAD mode) and adds
+// dt M Q L_rev z (ADJ mode).
 // The material enters L through Q^{-1} (per element) and through the face
 // impedances of the stabilisation (face-averaged medium); the second part is
 // accumulated per face node and chained to (rho, lambda, mu) at the end.
@@ -263,8 +264,13 @@ dgw_status dgw_receivers_adjoint(dgw_ctx* c, double* lam_u, const double* gv, vo
   return DGW_OK;
 }
 
-dgw_status dgw_adjoint_step(dgw_ctx* c, double* lam_u, double* lam_res, double* grad_mat, const double* u_ckpt,
-                            double t0, double dt, int nsteps, void* stream) {
+// The adjoint of nsteps steps from the checkpoint u_ckpt (with receiver-trace
+// sources g_traces[k] injected before the transpose of step k when g_traces is
+// not NULL).  The forward states are recomputed once, keeping every stage
+// input (5 nsteps states of scratch); the reverse sweep then runs, per stage,
+// the weight preparation and the fused GRAD + ADJ kernel.
+static dgw_status adjoint_segment(dgw_ctx* c, double* lam_u, double* lam_res, double* grad_mat, const double* u_ckpt,
+                                  const double* g_traces, double t0, double dt, int nsteps, cudaStream_t s) {
   if (!c) return afail(nullptr, DGW_ERR_ARG, "null context");
   if (c->cfg.system != DGW_SYSTEM_ELASTIC) return afail(c, DGW_ERR_UNSUPPORTED, "the adjoint is elastic only");
   if (!c->has_mesh || !c->has_material) return afail(c, DGW_ERR_STATE, "adjoint before mesh and material");
@@ -276,14 +282,17 @@ dgw_status dgw_adjoint_step(dgw_ctx* c, double* lam_u, double* lam_res, double* 
   for (const void* q : ptrs)
     if (!q || !dev_ptr(q)) return afail(c, DGW_ERR_ARG, "lam_u, lam_res, grad_mat and u_ckpt must be device buffers");
   if (lam_u == lam_res) return afail(c, DGW_ERR_ARG, "lam_u and lam_res must be distinct");
+  if (g_traces) {
+    if (c->rec_n == 0) return afail(c, DGW_ERR_STATE, "trace sources without receivers");
+    if (!dev_ptr(g_traces)) return afail(c, DGW_ERR_ARG, "g_traces must be a device buffer");
+  }
   if (cudaSetDevice(c->device) != cudaSuccess) return afail(c, DGW_ERR_CUDA, "cudaSetDevice");
-  cudaStream_t s = (cudaStream_t)stream;
   const int N = c->cfg.N, n = N + 1, Np = n * n * n, nf = n * n;
   const size_t state = (size_t)c->nel * Np * 9 * sizeof(double);
   const size_t nodes = (size_t)c->nel * Np;
-  // scratch: W, Z, forward register, 5 stage inputs, nsteps step starts, face terms
+  // scratch: W, Z, forward register, then the 5 stage inputs of every step
   dgw_status st;
-  if ((st = ensure(c, &c->adj_scratch, c->adj_scratch_bytes, state * (8 + (size_t)nsteps))) != DGW_OK) return st;
+  if ((st = ensure(c, &c->adj_scratch, c->adj_scratch_bytes, state * (3 + 5 * (size_t)nsteps))) != DGW_OK) return st;
   if ((st = ensure(c, &c->adj_gface, c->adj_gface_bytes, 2 * (size_t)c->nel * 6 * nf * sizeof(double))) != DGW_OK)
     return st;
   if (!c->etoe_d) {
@@ -299,67 +308,74 @@ dgw_status dgw_adjoint_step(dgw_ctx* c, double* lam_u, double* lam_res, double* 
   double* W = base;
   double* Z = base + 9 * nodes;
   double* fres = base + 2 * 9 * nodes;
-  double* ins[5];
-  for (int k = 0; k < 5; ++k) ins[k] = base + (3 + k) * 9 * nodes;
-  double* starts = base + 8 * 9 * nodes;
-  ACUDA(cudaMemsetAsync(c->adj_gface, 0, 2 * (size_t)c->nel * 6 * nf * sizeof(double), s), "clear face terms");
-  ACUDA(cudaMemcpyAsync(starts, u_ckpt, state, cudaMemcpyDeviceToDevice, s), "copy checkpoint");
-
-  auto forward_stage = [&](const double* uin, double* uout, double* res, int st_, double tstep) -> cudaError_t {
-    dgw::StageParams p = base_params(c);
-    p.u_in = uin;
-    p.out = uout;
-    p.res = res;
-    p.a = kA[st_];
-    p.b = kB[st_];
-    p.dt = dt;
-    p.src_amp = c->src_elem >= 0 ? ricker_h(tstep + kC[st_] * dt, c->src_f0, c->src_t0) : 0.0;
-    return dgw::launch_stage_fp64(N, true, p, s);
+  double* ins = base + 3 * 9 * nodes;
+  // input of stage st of step k: the checkpoint for (0, 0), else slot 5 k + st
+  auto input = [&](int k, int st_) -> double* {
+    return (k == 0 && st_ == 0) ? const_cast<double*>(u_ckpt) : ins + (size_t)(5 * k + st_) * 9 * nodes;
   };
-  // step starts of the segment
-  for (int k = 0; k + 1 < nsteps; ++k) {
-    double* cur = starts + (size_t)k * 9 * nodes;
-    double* nxt = starts + (size_t)(k + 1) * 9 * nodes;
-    ACUDA(cudaMemsetAsync(fres, 0, state, s), "clear register");
-    double* a = cur;
+  ACUDA(cudaMemsetAsync(c->adj_gface, 0, 2 * (size_t)c->nel * 6 * nf * sizeof(double), s), "clear face terms");
+
+  // forward recompute of the segment (the first stage of a step does not read
+  // the register, a_0 = 0); the last step's final state is not needed
+  for (int k = 0; k < nsteps; ++k) {
     for (int st_ = 0; st_ < 5; ++st_) {
-      double* b = (st_ == 4) ? nxt : ins[st_ % 2];
-      ACUDA(forward_stage(a, b, fres, st_, t0 + k * dt), "forward recompute");
-      a = b;
+      if (k == nsteps - 1 && st_ == 4) break;
+      dgw::StageParams p = base_params(c);
+      p.u_in = input(k, st_);
+      p.out = st_ < 4 ? input(k, st_ + 1) : input(k + 1, 0);
+      p.res = fres;
+      p.a = kA[st_];
+      p.b = kB[st_];
+      p.dt = dt;
+      p.src_amp = c->src_elem >= 0 ? ricker_h(t0 + k * dt + kC[st_] * dt, c->src_f0, c->src_t0) : 0.0;
+      ACUDA(dgw::launch_stage_fp64(N, true, p, s), "forward recompute");
     }
   }
   const int pblocks = c->sm_count * 8;
+  const int Np_ = Np;
   for (int k = nsteps - 1; k >= 0; --k) {
     const double tk = t0 + k * dt;
-    ACUDA(cudaMemcpyAsync(ins[0], starts + (size_t)k * 9 * nodes, state, cudaMemcpyDeviceToDevice, s), "stage input");
-    ACUDA(cudaMemsetAsync(fres, 0, state, s), "clear register");
-    for (int st_ = 0; st_ < 4; ++st_) ACUDA(forward_stage(ins[st_], ins[st_ + 1], fres, st_, tk), "forward recompute");
+    if (g_traces) {
+      dgw::receivers_adjoint_kernel<<<1, 128, 0, s>>>(lam_u, c->rec_elem, c->rec_w, g_traces + (size_t)k * c->rec_n * 3,
+                                                      c->rec_n, c->nel, Np_);
+      ACUDA(cudaGetLastError(), "receiver adjoint");
+    }
     for (int st_ = 4; st_ >= 0; --st_) {
       dgw::adjoint_prep_kernel<<<pblocks, 256, 0, s>>>(lam_u, lam_res, W, Z, static_cast<const double*>(c->mat),
                                                        c->wJ, c->nel, Np, kA[st_], kB[st_]);
       ACUDA(cudaGetLastError(), "adjoint preparation");
       dgw::StageParams g = base_params(c);
-      g.u_in = ins[st_];
+      g.u_in = input(k, st_);
       g.res = W;
       g.out = nullptr;
       g.dt = dt;
       g.grad_el = grad_mat;
       g.grad_face = c->adj_gface;
       g.src_amp = c->src_elem >= 0 ? ricker_h(tk + kC[st_] * dt, c->src_f0, c->src_t0) : 0.0;
-      ACUDA(dgw::launch_stage_adjoint(N, 3, g, s), "gradient terms");
       dgw::StageParams a = base_params(c);
       a.u_in = Z;
       a.res = lam_u;
       a.out = lam_u;
       a.dt = dt;
       a.src_elem = -1;
-      ACUDA(dgw::launch_stage_adjoint(N, 2, a, s), "adjoint stage");
+      ACUDA(dgw::launch_stage_adjgrad(N, g, a, s), "adjoint stage");
     }
   }
   dgw::adjoint_chain_kernel<<<(unsigned)((c->nel + 127) / 128), 128, 0, s>>>(
       c->adj_gface, c->etoe_d, c->etof_d, static_cast<const double*>(c->mat), c->nel, nf, grad_mat);
   ACUDA(cudaGetLastError(), "gradient chain");
   return DGW_OK;
+}
+
+dgw_status dgw_adjoint_step(dgw_ctx* c, double* lam_u, double* lam_res, double* grad_mat, const double* u_ckpt,
+                            double t0, double dt, int nsteps, void* stream) {
+  return adjoint_segment(c, lam_u, lam_res, grad_mat, u_ckpt, nullptr, t0, dt, nsteps, (cudaStream_t)stream);
+}
+
+dgw_status dgw_adjoint_traces(dgw_ctx* c, double* lam_u, double* lam_res, double* grad_mat, const double* u_ckpt,
+                              const double* g_traces, double t0, double dt, int nsteps, void* stream) {
+  if (c && !g_traces) return afail(c, DGW_ERR_ARG, "g_traces must be given (dgw_adjoint_step runs without)");
+  return adjoint_segment(c, lam_u, lam_res, grad_mat, u_ckpt, g_traces, t0, dt, nsteps, (cudaStream_t)stream);
 }
 
 }  // extern "C"

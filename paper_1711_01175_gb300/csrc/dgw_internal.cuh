@@ -135,6 +135,8 @@ cudaError_t launch_stage_mixed_tc(int N, int fmt, bool lsrk, const StageParams& 
 // Precisions whose geometry, face and material arrays are FP32.
 inline bool fp32_arrays(int precision) { return precision != DGW_PRECISION_FP64; }
 cudaError_t launch_stage_adjoint(int N, int mode, const StageParams& p, cudaStream_t s);   // mode 2: ADJ, 3: GRAD
+// GRAD (params g) then ADJ (params a) on every tile, in one launch.
+cudaError_t launch_stage_adjgrad(int N, const StageParams& g, const StageParams& a, cudaStream_t s);
 void stage_shape(int N, int* epb, int* threads);
 
 // Geometry (dgw_geometry.cu).

@@ -1093,6 +1093,55 @@ cudaError_t launch_stage_any(int N, bool lsrk, const StageParams& p, cudaStream_
 #undef DGW_CASE
 }
 
+// One adjoint stage in one launch: every CTA takes its tile in GRAD mode (the
+// forward operator on the stage input, gradient terms against the weight w),
+// then in ADJ mode (the reversed operator on z, added to lu).  The two modes
+// read the same metric terms, neighbour map, face impedances and medium of the
+// tile, which the second pass finds in cache; they write disjoint outputs.
+template <int N>
+__global__ void __launch_bounds__(Shape<N>::NT) stage_adjgrad_kernel(const StageParams g, const StageParams a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* D_s = reinterpret_cast<double*>(smem_raw + StageSmem<N, double>::d_off);
+  for (int i = threadIdx.x; i < Shape<N>::n * Shape<N>::n; i += Shape<N>::NT) D_s[i] = g.D[i];
+  stage_tile<N, double, kModeGrad>(g, blockIdx.x, smem_raw);
+  __syncthreads();
+  stage_tile<N, double, kModeAdj>(a, blockIdx.x, smem_raw);
+}
+
+template <int N>
+cudaError_t launch_stage_adjgrad_t(const StageParams& g, const StageParams& a, cudaStream_t s) {
+  const size_t smem = StageSmem<N, double>::bytes;
+  static std::atomic<unsigned long long> ready{0};
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
+  if (!(ready.load(std::memory_order_relaxed) & bit)) {
+    err = cudaFuncSetAttribute(stage_adjgrad_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    ready.fetch_or(bit, std::memory_order_relaxed);
+  }
+  const long long blocks = (g.nel + Shape<N>::EPB - 1) / Shape<N>::EPB;
+  if (blocks <= 0) return cudaSuccess;
+  StageParams gq = g, aq = a;
+  finish_stage_params(gq);
+  finish_stage_params(aq);
+  stage_adjgrad_kernel<N><<<(unsigned)blocks, Shape<N>::NT, smem, s>>>(gq, aq);
+  return cudaGetLastError();
+}
+
+inline cudaError_t launch_stage_adjgrad_any(int N, const StageParams& g, const StageParams& a, cudaStream_t s) {
+  switch (N) {
+#define DGW_GCASE(NN) \
+  case NN:            \
+    return launch_stage_adjgrad_t<NN>(g, a, s);
+    DGW_GCASE(1) DGW_GCASE(2) DGW_GCASE(3) DGW_GCASE(4) DGW_GCASE(5) DGW_GCASE(6) DGW_GCASE(7)
+#undef DGW_GCASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
 // Adjoint modes (FP64 only).
 inline cudaError_t launch_stage_adjoint_any(int N, int mode, const StageParams& p, cudaStream_t s) {
 #define DGW_ACASE(NN)                                                                                  \

@@ -26,6 +26,10 @@ cudaError_t launch_stage_adjoint(int N, int mode, const StageParams& p, cudaStre
   return launch_stage_adjoint_any(N, mode, p, s);
 }
 
+cudaError_t launch_stage_adjgrad(int N, const StageParams& g, const StageParams& a, cudaStream_t s) {
+  return launch_stage_adjgrad_any(N, g, a, s);
+}
+
 cudaError_t launch_stage_batch_fp64(int N, const BatchLaunch& L, const BatchSet& S, int grid, cudaStream_t s) {
   return launch_stage_batch_any<double>(N, L, S, grid, s);
 }

@@ -32,7 +32,7 @@ def bytes_per_request(E, N, precision):
     mass weights and the neighbour map."""
     nel = E ** 3
     Np = (N + 1) ** 3
-    real = 4 if precision == "mixed" else 8
+    real = 8 if precision == "fp64" else 4
     per_node = 3 * 9 * 8 + 10 * real + 8 + 6 * (N + 1) ** 2 * 4 / Np
     return int(nel * Np * per_node + nel * 200)
 

@@ -209,6 +209,13 @@ class Solver:
         self._check(capi.dgw_adjoint_step(self._ctx, _ptr(lam_u), _ptr(lam_res), _ptr(grad), _ptr(u_ckpt),
                                           float(t0), float(dt), int(nsteps), _stream_handle(stream)))
 
+    def adjoint_traces(self, lam_u, lam_res, grad, u_ckpt, g_traces, dt: float, nsteps: int, t0: float = 0.0,
+                       stream=None):
+        """Adjoint of the nsteps steps from u_ckpt at t0 with receiver-trace sources
+        g_traces [nsteps, nrec, 3] (device); grad [3, nel] is incremented."""
+        self._check(capi.dgw_adjoint_traces(self._ctx, _ptr(lam_u), _ptr(lam_res), _ptr(grad), _ptr(u_ckpt),
+                                            _ptr(g_traces), float(t0), float(dt), int(nsteps), _stream_handle(stream)))
+
     def dt_cfl(self) -> float:
         st, val = capi.dgw_dt_cfl(self._ctx)
         self._check(st)

@@ -144,3 +144,41 @@ def test_batch_rejects_mismatched_solves():
                             D(a["dt"], c["dt"]), D(0.0, 0.0), stream)
     assert st == -1 and "differs" in capi.dgw_batch_last_error(b.h)
     b.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batched_full_size_solve_sampled_oracle(precision):
+    """The largest solve of the serving recipe (48^3 elements, N=5, warp 0.1,
+    smooth random medium, Ricker point force at the centre element, free surface
+    on top, absorbing bottom) advanced by the batched kernel for one step pair
+    from a random state, against the oracle on sampled elements (the source
+    element, a free-surface and an absorbing element, an interior one), which
+    it evaluates exactly through the shrinking dependence regions of the ten
+    stages."""
+    import torch
+    from harness import oracle_sampled_steps
+    stream = torch.cuda.current_stream().cuda_stream
+    it = make_solve(48, 5, 11, precision)
+    it["u"] = torch.from_numpy(it["u0"]).cuda()
+    it["res"] = torch.zeros_like(it["u"])
+    b = Batch(5, precision)
+    b.set([it], [0.0], stream)
+    b.run(1, stream)
+    torch.cuda.synchronize()
+    m = it["mesh"]
+    rng = np.random.default_rng(3)
+    top = np.nonzero(m.bc[:, 5] == wl.BC_FREE_SURFACE)[0]
+    bottom = np.nonzero(m.bc[:, 4] == wl.BC_ABSORBING)[0]
+    sample = np.unique([it["src"]["element"], int(rng.choice(top)), int(rng.choice(bottom)), int(rng.integers(m.nel))])
+    r, _ = oracle.gll(5)
+    xo = wl.warped_node_coords(m, r, 0.1)
+    op = oracle.ElasticDG(5, xo, m.etoe, m.etof, m.orient, m.bc, *it["mat"], 1)
+    src = it["src"]
+    op.set_point_force(src["element"], src["xi"], src["force"], src["f0"], src["t0"])
+    uo, _ = oracle_sampled_steps(op, it["u0"], np.zeros_like(it["u0"]), it["dt"], 2, sample)
+    got = it["u"].cpu().numpy()[:, sample]
+    # the step pair changes u by O(dt |L u|): compare the increments
+    du_o = uo - it["u0"][:, sample]
+    assert_parity(got - it["u0"][:, sample], du_o, 1e-12 if precision == "fp64" else 1e-6,
+                  label=f"48^3 N=5 batched {precision} sampled")
+    b.close()
