@@ -177,6 +177,10 @@ def dgw_adjoint_step(ctx, lam_u, lam_res, grad_mat, u_ckpt, t0, dt, nsteps, stre
     return load().dgw_adjoint_step(ctx, lam_u, lam_res, grad_mat, u_ckpt, t0, dt, nsteps, stream)
 
 
+def dgw_adjoint_traces(ctx, lam_u, lam_res, grad_mat, u_ckpt, g_traces, t0, dt, nsteps, stream):
+    return load().dgw_adjoint_traces(ctx, lam_u, lam_res, grad_mat, u_ckpt, g_traces, t0, dt, nsteps, stream)
+
+
 def dgw_dt_cfl(ctx):
     out = _D()
     st = load().dgw_dt_cfl(ctx, ctypes.byref(out))

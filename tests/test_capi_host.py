@@ -38,6 +38,8 @@ def test_every_declared_symbol_is_exported(lib):
     for name in names:
         assert hasattr(lib, name), name
     assert sorted(capi.SIGNATURES) == names
+    for name in names:                       # a Python function of the same name for each
+        assert callable(getattr(capi, name, None)), name
 
 
 def test_abi_version(lib):
