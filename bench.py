@@ -54,9 +54,9 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def measured_traffic(precision):
-    """DRAM bytes per stage launch from the committed ncu summary, or None when the
-    stage-kernel sources changed since that capture."""
+def measured_traffic(precision, key=None):
+    """DRAM bytes per stage launch from the committed ncu summary (or another of
+    its keys), or None when the stage-kernel sources changed since that capture."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_1711_01175_gb300", "csrc")
     h = hashlib.sha256()
@@ -73,7 +73,7 @@ def measured_traffic(precision):
             vals[k] = v
     if vals.get("source_sha256") != h.hexdigest()[:16]:
         return None
-    v = vals.get(f"{precision}_bytes_per_launch")
+    v = vals.get(key or f"{precision}_bytes_per_launch")
     return float(v) if v is not None else None
 
 
@@ -200,6 +200,20 @@ def whole_job_rate(local_ms, local_units, device=None):
 def energy_reduction_launches(stage_ctas):
     """Kernels of the fused energy's final reduction (one block up to 2048 partials, two levels above)."""
     return 1 if stage_ctas <= 8 * 256 else 2
+
+
+def fp64_probe(device):
+    """The device's measured FP64 FMA rate (dgw_probe_fp64_rate), with the SM
+    clocks sampled while it runs."""
+    from paper_1711_01175_gb300 import capi
+    clk = Clocks(device.index or 0)
+    clk.start()
+    best = 0.0
+    for _ in range(3):
+        st, tf = capi.dgw_probe_fp64_rate(device.index or 0)
+        capi.check(st)
+        best = max(best, tf)
+    return {"tflops": best, "clocks": clk.stop()}
 
 
 def run_variant(precision, cfg, data, steps, warmup, device, stream, clocks=None):
@@ -408,6 +422,83 @@ def cpu_oracle_sample(cfg, data, target_s=12.0, nel_sample=512):
     return {"value": len(elems) * Np * 9 * stages / el, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{stages} LSRK stages on {len(elems)} of {m.nel} elements of {cfg.name} "
                       f"(numpy FP64, 1 thread), {el:.1f} s"}
+
+
+def _oracle_worker(args):
+    """One process of the all-cores oracle leg: attach the shared workload
+    arrays, build the oracle and time LSRK stages on its own block of elements
+    (the loops of all workers start at one barrier)."""
+    name, E, paths, mesh_arrays, mat, elems, target_s, barrier = args
+    import oracle
+    cfg = workload_config(name, E)
+    x, u = (np.load(p, mmap_mode="r") for p in paths)
+    etoe, etof, orient, bc = mesh_arrays
+    op = oracle.ElasticDG(cfg.N, x, etoe, etof, orient, bc, *mat, cfg.tau)
+    dt = oracle.cfl_dt(cfg.cfl, oracle.h_min_corner_edges(x, cfg.N), op.c_max(), cfg.N)
+    res = np.zeros_like(u)                   # pages stay untouched outside the block
+    op.lsrk_stage(u, res, 0, dt, elems)      # geometry of the block (set-up, untimed)
+    barrier.wait()
+    stages = 0
+    t0 = time.perf_counter()
+    while True:
+        for s_ in range(5):
+            op.lsrk_stage(u, res, s_, dt, elems)
+            stages += 1
+        if time.perf_counter() - t0 > target_s:
+            break
+    el = time.perf_counter() - t0
+    return stages, len(elems), el
+
+
+def cpu_oracle_all_cores(cfg, data, target_s=12.0, nel_block=256):
+    """The oracle, as it stands, on every host core: one spawned process per core,
+    each timing LSRK stages on its own block of elements of the same workload
+    (node coordinates and state memory-mapped from one file each, not copied).
+    Throughput = the sum of the processes' rates over their common timed
+    interval."""
+    import multiprocessing as mp
+    import shutil
+    import oracle
+    cores = os.cpu_count() or 1
+    m = data["mesh"]
+    r, _ = oracle.gll(cfg.N)
+    x = wl.warped_node_coords(m, r, cfg.amplitude)
+    tmp = tempfile.mkdtemp(prefix="dgw_oracle_")
+    try:
+        paths = []
+        for nm, a in (("x", x), ("u0", data["u0"])):
+            paths.append(os.path.join(tmp, nm + ".npy"))
+            np.save(paths[-1], a)
+        del x
+        ctx = mp.get_context("spawn")
+        with ctx.Manager() as mgr:
+            barrier = mgr.Barrier(cores)
+            jobs = [(cfg.name.split("-")[0], cfg.E, paths, (m.etoe, m.etof, m.orient, m.bc),
+                     (data["rho"], data["lam"], data["mu"]),
+                     np.arange(k * nel_block, (k + 1) * nel_block) % m.nel, target_s, barrier) for k in range(cores)]
+            with ctx.Pool(cores) as pool:
+                outs = pool.map(_oracle_worker, jobs)
+    finally:
+        shutil.rmtree(tmp, ignore_errors=True)
+    Np = (cfg.N + 1) ** 3
+    value = sum(st * ne * Np * 9 / el for st, ne, el in outs)
+    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{cores} processes x {nel_block} elements of {m.nel} ({cfg.name}), "
+                      f"{min(o[0] for o in outs)}-{max(o[0] for o in outs)} LSRK stages each in "
+                      f"{max(o[2] for o in outs):.1f} s (numpy FP64, 1 thread per process)",
+            "cpu_model": _cpu_model()}
+
+
+def _cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part", "hardware")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 def workload_name(cfg):
@@ -913,12 +1004,20 @@ def main():
         if prec == "fp64":
             flops = algorithmic_flops_per_element(N) * r["nel"]
             ach = flops / (r["stage_ms"] * 1e-3) / 1e12
+            probe = fp64_probe(device)
+            busy = measured_traffic("fp64", "fp64_pipe_busy_pct") if cfg.name == "large-64^3-N4" else None
             r["roofline"] = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                              "frac": ach / FP64_PEAK_TFLOPS,
                              "traffic": measured_traffic("fp64") if cfg.name == "large-64^3-N4" else None,
                              "kernel": f"stage_kernel<{N},double,LSRK>",
+                             "peak_measured": probe["tflops"], "frac_of_measured": ach / probe["tflops"],
+                             "fp64_pipe_busy_ncu": None if busy is None else busy / 100.0,
                              "note": "FP64 flops as written per launch / CUDA-event stage time; peak derived "
-                                     "from 152 SMs x 2 DFMA/clk x 2.07 GHz (nominal)"}
+                                     "from 152 SMs x 2 DFMA/clk x 2.07 GHz (nominal); peak_measured: "
+                                     "dgw_probe_fp64_rate (independent DFMA chains on every SM) in this run, "
+                                     f"SM clock median {probe['clocks']['sm_mhz']} MHz during the probe; "
+                                     "fp64_pipe_busy_ncu: sm__pipe_fp64_cycles_active of the committed ncu capture "
+                                     "(the figure of merit of a kernel bound by its FP64 pipe)"}
         else:
             r["roofline"] = mixed_roofline(prec, N, r, hbm_peak, peak_kind, cfg)
         results[prec] = r
@@ -946,6 +1045,8 @@ def main():
         line["e2e"] = head["e2e"]
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_sample(cfg, data)
+        line["cpu_baseline"]["cpu_model"] = _cpu_model()
+        line["cpu_baseline_all_cores"] = cpu_oracle_all_cores(cfg, data)
     if world == 1 and not args.no_serving:
         line["serving"] = run_serving(args)
     if world == 1 and not args.no_adjoint:

@@ -38,6 +38,7 @@
 #ifndef DGW_H
 #define DGW_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -362,6 +363,58 @@ dgw_status dgw_ihdg_setup(dgw_ctx* ctx, double sigma, void* stream);
  * dgw_ihdg_setup; DGW_ERR_UNSTABLE on a non-finite iterate. */
 dgw_status dgw_ihdg_solve(dgw_ctx* ctx, const double* u_prev, const double* f, double* u, double tol, int max_iter,
                           int* iterations, double* last_change, void* stream);
+
+/* ---- Checkpoint and resume ------------------------------------------------
+ * The paper's runs are not restarted; these calls serve long solves and the
+ * serving loop.  A checkpoint is a host byte buffer: an 80-byte header (magic,
+ * ABI version, degree, fields, element count, step, time, a fingerprint of the
+ * mesh and medium, an FNV-1a checksum of the payload), then u [m][nel][Np]
+ * and, optionally, the Runge-Kutta register (FP64, the layout of the field
+ * buffers).  Between steps the register is not needed (the first stage does
+ * not read it); inside a step sequence driven by dgw_stage it is. */
+
+/* Bytes of a checkpoint of this context's solve, with (with_res != 0) or
+ * without the register.  DGW_ERR_STATE before the mesh. */
+dgw_status dgw_state_bytes(dgw_ctx* ctx, int with_res, size_t* bytes);
+
+/* Write a checkpoint of (u, res, t, step) into the host buffer buf (buf_bytes
+ * at least dgw_state_bytes).  u, res: device or host field buffers; res NULL
+ * leaves the register out.  Synchronises `stream`.  DGW_ERR_ARG for a short
+ * buffer. */
+dgw_status dgw_get_state(dgw_ctx* ctx, const double* u, const double* res, double t, int64_t step, void* buf,
+                         size_t buf_bytes, void* stream);
+
+/* Load a checkpoint written by dgw_get_state into u (and res, unless NULL)
+ * and return its time and step (either pointer may be NULL).  The checkpoint
+ * must come from a context on the same mesh and medium (same degree, system,
+ * element count, connectivity, boundary tags, smallest edge and largest wave
+ * speed) with the same ABI, and its payload must match its checksum; otherwise
+ * DGW_ERR_ARG and nothing is copied.  Synchronises `stream`. */
+dgw_status dgw_set_state(dgw_ctx* ctx, const void* buf, size_t buf_bytes, double* u, double* res, double* t,
+                         int64_t* step, void* stream);
+
+/* ---- Debug build ----------------------------------------------------------
+ * Built with -DDGW_DEBUG_CHECKS (paper_1711_01175_gb300.build.build(debug=True),
+ * libdgw_debug.so; the Python binding loads it when the environment variable
+ * DGW_DEBUG_CHECKS=1), the stage kernels of dgw_rhs, dgw_stage and dgw_step
+ * check every state value they load (finite) and every neighbour index they
+ * follow (inside the mesh), record the first failing element and count the
+ * failures, and skip the read a bad index would make.  This call synchronises
+ * the device, returns the first fault since the previous call (code 0: none,
+ * 1: non-finite state, 2: neighbour index out of range; element: the element
+ * being computed) and the number of failed checks, and clears them.  Release
+ * builds return DGW_ERR_UNSUPPORTED.  Any pointer may be NULL. */
+dgw_status dgw_debug_status(dgw_ctx* ctx, int* code, int64_t* element, int64_t* count);
+
+/* Measurement helper; the paper has no counterpart.  The FP64 fused
+ * multiply-add rate of CUDA device `device` in TFLOP/s (2 flops per DFMA):
+ * eight independent DFMA chains per thread, 8 blocks of 256 threads per SM,
+ * 4096 iterations, timed with CUDA events on the legacy stream (the best of
+ * three launches after a warm-up).  It is the measured ceiling of the FP64
+ * path, whose stage kernel is bound by the FP64 pipe.  Allocates and frees a
+ * small device buffer and synchronises the device.  tflops: host double.
+ * Errors: dgw_last_error(NULL). */
+dgw_status dgw_probe_fp64_rate(int device, double* tflops);
 
 /* Message of the last failing call on ctx (or of the last failing call
  * without a context when ctx is NULL).  Never NULL; owned by the library. */

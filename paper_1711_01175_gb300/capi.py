@@ -11,6 +11,9 @@ import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libdgw.so")
+# the build with device-side checks (DGW_DEBUG_CHECKS); loaded when the
+# environment variable DGW_DEBUG_CHECKS is 1
+LIB_DEBUG_PATH = os.path.join(HERE, "libdgw_debug.so")
 
 DGW_OK = 0
 STATUS = {0: "DGW_OK", -1: "DGW_ERR_ARG", -2: "DGW_ERR_STATE", -3: "DGW_ERR_OOM", -4: "DGW_ERR_CUDA",
@@ -64,6 +67,11 @@ SIGNATURES = {
     "dgw_energy_static": (_I, [_I, _I64, _P, _P, _P, _P, _P, _P, _P]),
     "dgw_ihdg_setup": (_I, [_P, _D, _P]),
     "dgw_ihdg_solve": (_I, [_P, _P, _P, _P, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), _P]),
+    "dgw_probe_fp64_rate": (_I, [_I, ctypes.POINTER(_D)]),
+    "dgw_debug_status": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
+    "dgw_state_bytes": (_I, [_P, _I, ctypes.POINTER(ctypes.c_size_t)]),
+    "dgw_get_state": (_I, [_P, _P, _P, _D, _I64, _P, ctypes.c_size_t, _P]),
+    "dgw_set_state": (_I, [_P, _P, ctypes.c_size_t, _P, _P, ctypes.POINTER(_D), ctypes.POINTER(_I64), _P]),
     "dgw_last_error": (ctypes.c_char_p, [_P]),
 }
 
@@ -76,11 +84,14 @@ class DGWError(RuntimeError):
         self.status = status
 
 
-def load(path: str = LIB_PATH):
-    """Load libdgw.so (built by ``paper_1711_01175_gb300.build.build()``)."""
+def load(path: str = None):
+    """Load libdgw.so (built by ``paper_1711_01175_gb300.build.build()``), or
+    libdgw_debug.so (``build(debug=True)``) when DGW_DEBUG_CHECKS=1."""
     global _lib
     if _lib is not None:
         return _lib
+    if path is None:
+        path = LIB_DEBUG_PATH if os.environ.get("DGW_DEBUG_CHECKS") == "1" else LIB_PATH
     if not os.path.exists(path):
         raise RuntimeError(f"{path} is missing: build the CUDA library first "
                            "(python -c 'import __graft_entry__ as g; g.build()')")
@@ -179,6 +190,34 @@ def dgw_adjoint_step(ctx, lam_u, lam_res, grad_mat, u_ckpt, t0, dt, nsteps, stre
 
 def dgw_adjoint_traces(ctx, lam_u, lam_res, grad_mat, u_ckpt, g_traces, t0, dt, nsteps, stream):
     return load().dgw_adjoint_traces(ctx, lam_u, lam_res, grad_mat, u_ckpt, g_traces, t0, dt, nsteps, stream)
+
+
+def dgw_probe_fp64_rate(device):
+    out = _D()
+    st = load().dgw_probe_fp64_rate(device, ctypes.byref(out))
+    return st, out.value
+
+
+def dgw_state_bytes(ctx, with_res):
+    out = ctypes.c_size_t()
+    st = load().dgw_state_bytes(ctx, int(with_res), ctypes.byref(out))
+    return st, out.value
+
+
+def dgw_get_state(ctx, u, res, t, step, buf, buf_bytes, stream):
+    return load().dgw_get_state(ctx, u, res, t, step, buf, buf_bytes, stream)
+
+
+def dgw_set_state(ctx, buf, buf_bytes, u, res, stream):
+    t, step = _D(), _I64()
+    st = load().dgw_set_state(ctx, buf, buf_bytes, u, res, ctypes.byref(t), ctypes.byref(step), stream)
+    return st, t.value, step.value
+
+
+def dgw_debug_status(ctx):
+    code, el, cnt = _I(), _I64(), _I64()
+    st = load().dgw_debug_status(ctx, ctypes.byref(code), ctypes.byref(el), ctypes.byref(cnt))
+    return st, code.value, el.value, cnt.value
 
 
 def dgw_dt_cfl(ctx):

@@ -369,11 +369,13 @@ static dgw_status adjoint_segment(dgw_ctx* c, double* lam_u, double* lam_res, do
 
 dgw_status dgw_adjoint_step(dgw_ctx* c, double* lam_u, double* lam_res, double* grad_mat, const double* u_ckpt,
                             double t0, double dt, int nsteps, void* stream) {
+  dgw::NvtxRange nvtx_range("dgw_adjoint_step");
   return adjoint_segment(c, lam_u, lam_res, grad_mat, u_ckpt, nullptr, t0, dt, nsteps, (cudaStream_t)stream);
 }
 
 dgw_status dgw_adjoint_traces(dgw_ctx* c, double* lam_u, double* lam_res, double* grad_mat, const double* u_ckpt,
                               const double* g_traces, double t0, double dt, int nsteps, void* stream) {
+  dgw::NvtxRange nvtx_range("dgw_adjoint_traces");
   if (c && !g_traces) return afail(c, DGW_ERR_ARG, "g_traces must be given (dgw_adjoint_step runs without)");
   return adjoint_segment(c, lam_u, lam_res, grad_mat, u_ckpt, g_traces, t0, dt, nsteps, (cudaStream_t)stream);
 }

@@ -214,6 +214,7 @@ dgw_status dgw_batch_destroy(dgw_batch* b) {
 
 dgw_status dgw_batch_set(dgw_batch* b, int n, dgw_ctx* const* ctxs, double* const* u, double* const* res,
                          const double* dt, const double* t0, void* stream) {
+  dgw::NvtxRange nvtx_range("dgw_batch_set");
   if (!b) return bfail(nullptr, DGW_ERR_ARG, "null batch");
   if (n < 0 || (n > 0 && (!ctxs || !u || !res || !dt || !t0))) return bfail(b, DGW_ERR_ARG, "bad arguments");
   if (cudaSetDevice(b->device) != cudaSuccess) return bfail(b, DGW_ERR_CUDA, "cudaSetDevice failed");
@@ -280,6 +281,7 @@ dgw_status dgw_batch_set(dgw_batch* b, int n, dgw_ctx* const* ctxs, double* cons
 }
 
 dgw_status dgw_batch_run(dgw_batch* b, int npairs, void* stream) {
+  dgw::NvtxRange nvtx_range("dgw_batch_run");
   if (!b) return bfail(nullptr, DGW_ERR_ARG, "null batch");
   if (npairs < 0) return bfail(b, DGW_ERR_ARG, "npairs must be >= 0");
   if (b->nsolves == 0 || npairs == 0) return DGW_OK;

@@ -111,6 +111,7 @@ dgw_status launch_stage(dgw_ctx* c, const double* u_in, double* out, double* res
   }
   p.src_elem = c->src_elem;
   p.src_w = c->src_w;
+  p.fault = c->fault;
   p.src_amp = c->src_elem >= 0 ? ricker(t_stage, c->src_f0, c->src_t0) : 0.0;
   p.energy_partials = energy_partials;
   p.wJ = c->wJ;
@@ -277,6 +278,13 @@ dgw_status dgw_create(dgw_ctx** out, int device, const dgw_config* cfg) {
     delete c;
     return fail(nullptr, DGW_ERR_CUDA, "set-up stream");
   }
+  if (cudaMalloc(&c->fault, 2 * sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMemset(c->fault, 0, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+    cudaStreamDestroy(c->setup);
+    if (c->fault) cudaFree(c->fault);
+    delete c;
+    return fail(nullptr, DGW_ERR_CUDA, "fault word");
+  }
   *out = c;
   return DGW_OK;
 }
@@ -286,12 +294,28 @@ dgw_status dgw_destroy(dgw_ctx* c) {
   cudaSetDevice(c->device);
   free_mesh(c);
   if (c->setup) cudaStreamDestroy(c->setup);
+  if (c->fault) cudaFree(c->fault);
   delete c;
+  return DGW_OK;
+}
+
+dgw_status dgw_debug_status(dgw_ctx* c, int* code, int64_t* element, int64_t* count) {
+  if (!c) return fail(nullptr, DGW_ERR_ARG, "null context");
+  if (!dgw::kDebugChecks) return fail(c, DGW_ERR_UNSUPPORTED, "library built without DGW_DEBUG_CHECKS");
+  if (set_device(c) != DGW_OK) return DGW_ERR_CUDA;
+  unsigned long long f[2] = {0, 0};
+  DGW_CUDA(c, cudaDeviceSynchronize(), "debug status");
+  DGW_CUDA(c, cudaMemcpy(f, c->fault, sizeof f, cudaMemcpyDeviceToHost), "debug status");
+  DGW_CUDA(c, cudaMemset(c->fault, 0, sizeof f), "debug status");
+  if (code) *code = (int)(f[0] >> 56);
+  if (element) *element = (int64_t)(f[0] & ((1ull << 56) - 1));
+  if (count) *count = (int64_t)f[1];
   return DGW_OK;
 }
 
 dgw_status dgw_mesh_upload(dgw_ctx* c, int64_t nel, const double* x, const int64_t* etoe,
                            const int8_t* etof, const int8_t* orient, const int8_t* bc) {
+  dgw::NvtxRange nvtx_range("dgw_mesh_upload");
   if (!c) return fail(nullptr, DGW_ERR_ARG, "null context");
   if (!x || !etoe || !etof || !orient || !bc) return fail(c, DGW_ERR_ARG, "null mesh array");
   const int N = c->cfg.N, n = N + 1, Np = Np_of(N), nf = n * n;
@@ -458,6 +482,7 @@ dgw_status dgw_mesh_upload(dgw_ctx* c, int64_t nel, const double* x, const int64
 }
 
 dgw_status dgw_material_upload(dgw_ctx* c, const double* rho, const double* lam, const double* mu) {
+  dgw::NvtxRange nvtx_range("dgw_material_upload");
   if (!c) return fail(nullptr, DGW_ERR_ARG, "null context");
   if (c->cfg.system != DGW_SYSTEM_ELASTIC)
     return fail(c, DGW_ERR_UNSUPPORTED, "transport and shallow water have no medium (Q = I)");
@@ -531,6 +556,7 @@ static dgw_status ensure_staging(dgw_ctx* c, bool need_res) {
 }
 
 dgw_status dgw_rhs(dgw_ctx* c, const double* u, double* rhs, double t, void* stream) {
+  dgw::NvtxRange nvtx_range("dgw_rhs");
   dgw_status st = ready(c);
   if (st != DGW_OK) return st;
   if (!u || !rhs || (const void*)u == (void*)rhs) return fail(c, DGW_ERR_ARG, "u and rhs must be distinct non-null buffers");
@@ -549,6 +575,7 @@ dgw_status dgw_rhs(dgw_ctx* c, const double* u, double* rhs, double t, void* str
 
 dgw_status dgw_stage(dgw_ctx* c, const double* u_in, double* u_out, double* res, int stage, double t,
                      double dt, void* stream) {
+  dgw::NvtxRange nvtx_range("dgw_stage");
   dgw_status st = ready(c);
   if (st != DGW_OK) return st;
   if (stage < 0 || stage > 4) return fail(c, DGW_ERR_ARG, "stage %d outside 0..4", stage);
@@ -564,6 +591,7 @@ dgw_status dgw_stage(dgw_ctx* c, const double* u_in, double* u_out, double* res,
 
 dgw_status dgw_stage_energy(dgw_ctx* c, const double* u_in, double* u_out, double* res, int stage, double t,
                             double dt, double* energy_out, void* stream) {
+  dgw::NvtxRange nvtx_range("dgw_stage_energy");
   dgw_status st = ready(c);
   if (st != DGW_OK) return st;
   if (stage < 0 || stage > 4) return fail(c, DGW_ERR_ARG, "stage %d outside 0..4", stage);
@@ -656,16 +684,19 @@ dgw_status step_impl(dgw_ctx* c, double* u, double* res, double t0, double dt, i
 extern "C" {
 
 dgw_status dgw_step(dgw_ctx* c, double* u, double* res, double t0, double dt, int nsteps, void* stream) {
+  dgw::NvtxRange nvtx_range("dgw_step");
   return step_impl(c, u, res, t0, dt, nsteps, nullptr, stream);
 }
 
 dgw_status dgw_step_energy(dgw_ctx* c, double* u, double* res, double t0, double dt, int nsteps,
                            double* energy_out, void* stream) {
+  dgw::NvtxRange nvtx_range("dgw_step_energy");
   if (!energy_out) return fail(c, DGW_ERR_ARG, "null energy_out");
   return step_impl(c, u, res, t0, dt, nsteps, energy_out, stream);
 }
 
 dgw_status dgw_energy(dgw_ctx* c, const double* u, double* energy_out, void* stream) {
+  dgw::NvtxRange nvtx_range("dgw_energy");
   dgw_status st = ready(c);
   if (st != DGW_OK) return st;
   if (!u || !energy_out) return fail(c, DGW_ERR_ARG, "null argument");

@@ -474,6 +474,7 @@ void ihdg_release(dgw_ctx* c) { ihdg_free(c); }
 extern "C" {
 
 dgw_status dgw_ihdg_setup(dgw_ctx* c, double sigma, void* stream) {
+  dgw::NvtxRange nvtx_range("dgw_ihdg_setup");
   if (!c) return dgw::ifail(nullptr, DGW_ERR_ARG, "null context");
   const bool elastic = c->cfg.system == DGW_SYSTEM_ELASTIC;
   if (elastic && c->cfg.precision != DGW_PRECISION_FP64)
@@ -597,6 +598,7 @@ dgw_status dgw_ihdg_setup(dgw_ctx* c, double sigma, void* stream) {
 
 dgw_status dgw_ihdg_solve(dgw_ctx* c, const double* u_prev, const double* f, double* u, double tol, int max_iter,
                           int* iterations, double* last_change, void* stream) {
+  dgw::NvtxRange nvtx_range("dgw_ihdg_solve");
   if (!c) return dgw::ifail(nullptr, DGW_ERR_ARG, "null context");
   if (!c->ihdg_ready) return dgw::ifail(c, DGW_ERR_STATE, "dgw_ihdg_setup first");
   if (!u || !iterations || max_iter < 1 || !(tol >= 0.0)) return dgw::ifail(c, DGW_ERR_ARG, "bad arguments");

@@ -7,9 +7,20 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "dgw.h"
 
 namespace dgw {
+
+// NVTX range over one library call (header-only NVTX3: inert unless a
+// profiler such as Nsight Systems or ncu --nvtx is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 constexpr int kMaxN = 7;
 constexpr int kFields = 9;
@@ -36,6 +47,23 @@ struct Shape {
   static constexpr int NT = ((NTILE + 31) / 32) * 32;
   static constexpr int NFACE_ITEMS = EPB * 6 * nf;
 };
+
+// Device-side checks of the debug build (compiled with -DDGW_DEBUG_CHECKS): a
+// stage kernel records the first fault it meets in the context's fault word
+// (code << 56 | element) and counts them, and skips the access a bad index
+// would make instead of performing it.
+#ifdef DGW_DEBUG_CHECKS
+constexpr bool kDebugChecks = true;
+#else
+constexpr bool kDebugChecks = false;
+#endif
+enum { kFaultNone = 0, kFaultNonFiniteState = 1, kFaultNeighbourIndex = 2 };
+
+__device__ __forceinline__ void debug_record(unsigned long long* fault, int code, long long element) {
+  if (fault == nullptr) return;
+  atomicAdd(fault + 1, 1ull);
+  atomicCAS(fault, 0ull, (static_cast<unsigned long long>(code) << 56) | static_cast<unsigned long long>(element));
+}
 
 // Neighbour-map sentinels for boundary faces (the map holds e*Np + node otherwise).
 constexpr int kGhostFreeSurface = -1;
@@ -70,6 +98,7 @@ struct StageParams {
   int first;
   double beta[3];           // transport velocity (generic-system kernel only)
   int self_only;            // generic-system kernel: neighbour states taken as zero (L_K^self)
+  unsigned long long* fault;  // debug build: [first fault, count] (NULL: not recorded)
   double D[(kMaxN + 1) * (kMaxN + 1)];
 };
 
@@ -192,6 +221,7 @@ struct dgw_ctx {
   double* u2 = nullptr;      // second state buffer for the stage ping-pong
   double* partials = nullptr;  // energy partial sums + result slot
   double* stage_partials = nullptr;  // per-CTA energy partials of a fused stage, result slot, reduction scratch
+  unsigned long long* fault = nullptr;  // debug build: [first fault, count] of the stage kernels
   int stage_ctas = 0;
   double* stage_u = nullptr;   // host-pointer staging buffers
   double* stage_res = nullptr;

@@ -436,6 +436,12 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
       for (int q = 0; q < 9; ++q) w[q] = to_real<Real>(p.u_in[q * fstride + gidx]);
 #pragma unroll
       for (int c = 0; c < 10; ++c) gj[c] = geo[c * fstride + gidx];
+      if constexpr (kDebugChecks) {
+        bool finite = true;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) finite = finite && isfinite(w[q]);
+        if (!finite) debug_record(p.fault, kFaultNonFiniteState, e);
+      }
     } else {
 #pragma unroll
       for (int c = 0; c < 10; ++c) w[c] = gj[c] = 0;
@@ -618,7 +624,13 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
 
       Real um[10], du[9];
       V::load9(u_s + sidx * PK, um);
-      const int g = p.vmapP[static_cast<size_t>(ei) * 6 * nf + r];
+      int g = p.vmapP[static_cast<size_t>(ei) * 6 * nf + r];
+      if constexpr (kDebugChecks) {
+        if (g >= 0 && static_cast<long long>(g) >= p.nel * Np) {
+          debug_record(p.fault, kFaultNeighbourIndex, ei);
+          g = kGhostAbsorbing;            // skip the out-of-range read
+        }
+      }
       // FP32 tiles of several elements (N <= 3): a neighbour node inside this
       // tile is read from the shared state tile (the same narrowed values) instead
       // of L2 (mixed N = 2: +5 %; the FP64 path, bound by its FP64 pipe, lost 2-3 %

@@ -216,6 +216,23 @@ class Solver:
         self._check(capi.dgw_adjoint_traces(self._ctx, _ptr(lam_u), _ptr(lam_res), _ptr(grad), _ptr(u_ckpt),
                                             _ptr(g_traces), float(t0), float(dt), int(nsteps), _stream_handle(stream)))
 
+    def get_state(self, u, res=None, t: float = 0.0, step: int = 0, stream=None):
+        """Checkpoint of (u, res, t, step) as a host uint8 array (dgw_get_state)."""
+        st, nbytes = capi.dgw_state_bytes(self._ctx, res is not None)
+        self._check(st)
+        buf = np.empty(nbytes, dtype=np.uint8)
+        self._check(capi.dgw_get_state(self._ctx, _ptr(u), None if res is None else _ptr(res), float(t), int(step),
+                                       _ptr(buf), nbytes, _stream_handle(stream)))
+        return buf
+
+    def set_state(self, buf, u, res=None, stream=None):
+        """Load a checkpoint into u (and res); returns its (t, step) (dgw_set_state)."""
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        st, t, step = capi.dgw_set_state(self._ctx, _ptr(buf), buf.nbytes, _ptr(u),
+                                         None if res is None else _ptr(res), _stream_handle(stream))
+        self._check(st)
+        return t, step
+
     def dt_cfl(self) -> float:
         st, val = capi.dgw_dt_cfl(self._ctx)
         self._check(st)

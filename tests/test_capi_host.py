@@ -142,3 +142,18 @@ def test_create_refuses_unknown_precision(lib):
         cfg = capi.dgw_config(3, 1, prec, 0.5, 0, (ctypes.c_double * 3)(0, 0, 0))
         st, _ = capi.dgw_create(0, cfg)
         assert st == -1 and "precision" in capi.dgw_last_error(None)
+
+
+def test_state_calls_refuse_missing_context(lib):
+    """Checkpoint calls need a context with a mesh (no GPU needed to see the refusal)."""
+    from paper_1711_01175_gb300 import capi
+    st, _ = capi.dgw_state_bytes(None, 1)
+    assert st == -1
+    buf = np.zeros(128, dtype=np.uint8)
+    st, _, _ = capi.dgw_set_state(None, buf.ctypes.data, buf.nbytes, buf.ctypes.data, None, None)
+    assert st == -1 and "context" in capi.dgw_last_error(None)
+
+
+def test_debug_status_refuses_missing_context(lib):
+    from paper_1711_01175_gb300 import capi
+    assert capi.dgw_debug_status(None)[0] == -1
