@@ -658,6 +658,9 @@ def run_adjoint(args):
             "gradient_norm": float(np.linalg.norm(g)),
             "gradient_share_source_and_neighbours": float(g2[:, near].sum() / g2.sum()),
             "gradient_share_within_two_faces": float(g2[:, around].sum() / g2.sum()),
+            "adjoint_scratch": ("stage inputs only, operator recomputed in the gradient terms (3 + 5 K states)"
+                                if os.environ.get("DGW_ADJOINT_LOW_MEMORY") == "1" else
+                                "stage inputs and stage operator outputs (3 + 10 K states, K = checkpoint interval)"),
             "precision": "fp64"}
 
 

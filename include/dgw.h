@@ -214,8 +214,8 @@ dgw_status dgw_source_set(dgw_ctx* ctx, int64_t element, const double* xi, const
  * on Q^{-1}, on the face impedances of the stabilisation and on the point
  * force.  The transpose uses L^T = (M Q) L_rev (M Q)^{-1}, L_rev the operator
  * with A_k -> -A_k (the upwind stabilisation of eq. RiemannFluxBoth is
- * symmetric and unchanged).  Stage inputs are recomputed from u_ckpt (once,
- * all of them kept: (3 + 5 nsteps) state-sized buffers of context scratch).
+ * symmetric and unchanged).  Stage inputs are recomputed from u_ckpt (once;
+ * scratch as for dgw_adjoint_traces).
  * Adjoint sources between steps need either nsteps = 1 per call with
  * dgw_receivers_adjoint between calls, or dgw_adjoint_traces.
  * Elastic FP64 contexts only (DGW_ERR_UNSUPPORTED otherwise). */
@@ -228,10 +228,14 @@ dgw_status dgw_adjoint_step(dgw_ctx* ctx, double* lam_u, double* lam_res, double
  * receiver sampling of dgw_receivers_sample applied to the state after step k.
  * g_traces: device [nsteps][nrec][3], the misfit's derivative with respect to
  * the traces.  One call covers a whole checkpoint segment: the forward states
- * are recomputed once from u_ckpt, keeping every stage input, which takes
- * (3 + 5 nsteps) state-sized device buffers of context scratch (released with
- * the context); DGW_ERR_OOM if they do not fit (use shorter segments).  Both
- * adjoint calls share that scratch and reach it through the same recompute.
+ * are recomputed once from u_ckpt, keeping every stage input and every
+ * stage's operator output dt (K u + f) (before Q^{-1}), which the gradient
+ * terms then read instead of applying the operator again: (3 + 10 nsteps)
+ * state-sized device buffers of context scratch (released with the context).
+ * If those do not fit, or the environment variable DGW_ADJOINT_LOW_MEMORY is
+ * 1, only the stage inputs are kept ((3 + 5 nsteps) buffers) and the gradient
+ * terms recompute the operator; DGW_ERR_OOM if even those do not fit (use
+ * shorter segments).  Both adjoint calls share that scratch.
  * DGW_ERR_STATE without receivers; otherwise as dgw_adjoint_step. */
 dgw_status dgw_adjoint_traces(dgw_ctx* ctx, double* lam_u, double* lam_res, double* grad_mat, const double* u_ckpt,
                               const double* g_traces, double t0, double dt, int nsteps, void* stream);
@@ -387,8 +391,8 @@ dgw_status dgw_get_state(dgw_ctx* ctx, const double* u, const double* res, doubl
 /* Load a checkpoint written by dgw_get_state into u (and res, unless NULL)
  * and return its time and step (either pointer may be NULL).  The checkpoint
  * must come from a context on the same mesh and medium (same degree, system,
- * element count, connectivity, boundary tags, smallest edge and largest wave
- * speed) with the same ABI, and its payload must match its checksum; otherwise
+ * element count, connectivity, boundary tags, smallest edge, largest wave
+ * speed and uploaded medium) with the same ABI, and its payload must match its checksum; otherwise
  * DGW_ERR_ARG and nothing is copied.  Synchronises `stream`. */
 dgw_status dgw_set_state(dgw_ctx* ctx, const void* buf, size_t buf_bytes, double* u, double* res, double* t,
                          int64_t* step, void* stream);

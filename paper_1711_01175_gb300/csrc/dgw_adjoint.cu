@@ -15,6 +15,7 @@
 // impedances of the stabilisation (face-averaged medium); the second part is
 // accumulated per face node and chained to (rho, lambda, mu) at the end.
 #include <cmath>
+#include <cstdlib>
 #include <string>
 #include <vector>
 
@@ -267,8 +268,10 @@ dgw_status dgw_receivers_adjoint(dgw_ctx* c, double* lam_u, const double* gv, vo
 // The adjoint of nsteps steps from the checkpoint u_ckpt (with receiver-trace
 // sources g_traces[k] injected before the transpose of step k when g_traces is
 // not NULL).  The forward states are recomputed once, keeping every stage
-// input (5 nsteps states of scratch); the reverse sweep then runs, per stage,
-// the weight preparation and the fused GRAD + ADJ kernel.
+// input and, when the scratch fits, every stage's operator output dt (K u + f)
+// (10 nsteps states; else 5 nsteps and the gradient terms recompute the
+// operator); the reverse sweep then runs, per stage, the weight preparation
+// and the fused GRAD + ADJ kernel.
 static dgw_status adjoint_segment(dgw_ctx* c, double* lam_u, double* lam_res, double* grad_mat, const double* u_ckpt,
                                   const double* g_traces, double t0, double dt, int nsteps, cudaStream_t s) {
   if (!c) return afail(nullptr, DGW_ERR_ARG, "null context");
@@ -290,9 +293,18 @@ static dgw_status adjoint_segment(dgw_ctx* c, double* lam_u, double* lam_res, do
   const int N = c->cfg.N, n = N + 1, Np = n * n * n, nf = n * n;
   const size_t state = (size_t)c->nel * Np * 9 * sizeof(double);
   const size_t nodes = (size_t)c->nel * Np;
-  // scratch: W, Z, forward register, then the 5 stage inputs of every step
+  // scratch: W, Z, forward register, the 5 stage inputs of every step, then
+  // (when it fits) the 5 stage outputs dt (K u + f) of every step
   dgw_status st;
-  if ((st = ensure(c, &c->adj_scratch, c->adj_scratch_bytes, state * (3 + 5 * (size_t)nsteps))) != DGW_OK) return st;
+  const char* low = std::getenv("DGW_ADJOINT_LOW_MEMORY");
+  bool keep_out = !(low && low[0] == '1');
+  if (!keep_out ||
+      ensure(c, &c->adj_scratch, c->adj_scratch_bytes, state * (3 + 10 * (size_t)nsteps)) != DGW_OK) {
+    cudaGetLastError();
+    keep_out = false;
+    if ((st = ensure(c, &c->adj_scratch, c->adj_scratch_bytes, state * (3 + 5 * (size_t)nsteps))) != DGW_OK)
+      return st;
+  }
   if ((st = ensure(c, &c->adj_gface, c->adj_gface_bytes, 2 * (size_t)c->nel * 6 * nf * sizeof(double))) != DGW_OK)
     return st;
   if (!c->etoe_d) {
@@ -313,16 +325,23 @@ static dgw_status adjoint_segment(dgw_ctx* c, double* lam_u, double* lam_res, do
   auto input = [&](int k, int st_) -> double* {
     return (k == 0 && st_ == 0) ? const_cast<double*>(u_ckpt) : ins + (size_t)(5 * k + st_) * 9 * nodes;
   };
+  double* outs = ins + (size_t)5 * nsteps * 9 * nodes;
+  auto output = [&](int k, int st_) -> double* {
+    return keep_out ? outs + (size_t)(5 * k + st_) * 9 * nodes : nullptr;
+  };
   ACUDA(cudaMemsetAsync(c->adj_gface, 0, 2 * (size_t)c->nel * 6 * nf * sizeof(double), s), "clear face terms");
 
   // forward recompute of the segment (the first stage of a step does not read
-  // the register, a_0 = 0); the last step's final state is not needed
+  // the register, a_0 = 0); the last step's final state is not needed (its
+  // last stage runs only for its operator output, into W)
   for (int k = 0; k < nsteps; ++k) {
     for (int st_ = 0; st_ < 5; ++st_) {
-      if (k == nsteps - 1 && st_ == 4) break;
+      const bool last = k == nsteps - 1 && st_ == 4;
+      if (last && !keep_out) break;
       dgw::StageParams p = base_params(c);
       p.u_in = input(k, st_);
-      p.out = st_ < 4 ? input(k, st_ + 1) : input(k + 1, 0);
+      p.out = last ? W : (st_ < 4 ? input(k, st_ + 1) : input(k + 1, 0));
+      p.rout = output(k, st_);
       p.res = fres;
       p.a = kA[st_];
       p.b = kB[st_];
@@ -351,6 +370,7 @@ static dgw_status adjoint_segment(dgw_ctx* c, double* lam_u, double* lam_res, do
       g.dt = dt;
       g.grad_el = grad_mat;
       g.grad_face = c->adj_gface;
+      g.rout = output(k, st_);
       g.src_amp = c->src_elem >= 0 ? ricker_h(tk + kC[st_] * dt, c->src_f0, c->src_t0) : 0.0;
       dgw::StageParams a = base_params(c);
       a.u_in = Z;

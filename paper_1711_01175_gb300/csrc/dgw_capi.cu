@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
 #include <string>
 #include <vector>
 
@@ -544,6 +545,17 @@ dgw_status dgw_material_upload(dgw_ctx* c, const double* rho, const double* lam,
   }
   DGW_CUDA(c, cudaStreamSynchronize(c->setup), "material upload");
   c->c_max = cmax;
+  {
+    uint64_t h = 1469598103934665603ull;       // FNV-1a over the three arrays' bytes
+    for (const double* a : {rho, lam, mu}) {
+      const unsigned char* b = reinterpret_cast<const unsigned char*>(a);
+      for (size_t i = 0; i < (size_t)nel * sizeof(double); ++i) {
+        h ^= b[i];
+        h *= 1099511628211ull;
+      }
+    }
+    c->medium_hash = h;
+  }
   c->has_material = true;
   return DGW_OK;
 }

@@ -99,6 +99,8 @@ struct StageParams {
   double beta[3];           // transport velocity (generic-system kernel only)
   int self_only;            // generic-system kernel: neighbour states taken as zero (L_K^self)
   unsigned long long* fault;  // debug build: [first fault, count] (NULL: not recorded)
+  double* rout;             // FP64 LSRK mode, optional: dt (K u + f) before Q^{-1} [9][nel][Np];
+                            // GRAD_FACE mode: read from there
   double D[(kMaxN + 1) * (kMaxN + 1)];
 };
 
@@ -243,6 +245,7 @@ struct dgw_ctx {
   signed char* etof_d = nullptr;
   double h_min = 0.0;
   double c_max = 0.0;
+  uint64_t medium_hash = 0;          // FNV-1a of the uploaded (rho, lambda, mu) (checkpoint fingerprint)
   // iHDG-II (transport): inverses of sigma I - L_K^self, transposed, and the
   // neighbour-coupling coefficient of every face node
   double* ihdg_inv = nullptr;        // [nel][Np][Np], entry (e, j, i) = inverse(e)[i][j]

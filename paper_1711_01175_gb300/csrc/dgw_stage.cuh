@@ -356,13 +356,16 @@ __device__ __forceinline__ void tc_contract(float* X, unsigned bhi, unsigned blo
 //   which together apply dt L^T w (L^T = (M Q) L_rev (M Q)^{-1}).
 // GRAD: the forward operator on a stage input u, accumulating the material
 //   gradient terms dt w^T (dL/dm) u of the adjoint weight w.
-enum { kModeRhs = 0, kModeLsrk = 1, kModeAdj = 2, kModeGrad = 3 };
+// GRAD_FACE: GRAD with the operator output taken from p.rout (written by the
+//   forward LSRK stage on the same input): only the face terms are computed.
+enum { kModeRhs = 0, kModeLsrk = 1, kModeAdj = 2, kModeGrad = 3, kModeGradFace = 4 };
 
 // One tile (EPB consecutive elements) of one solve.  The caller has filled the
 // D tile of shared memory; p may live in parameter or shared memory.
 template <int N, typename Real, int MODE, int VOL = kVolCuda>
 __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile, unsigned char* smem_raw) {
   constexpr bool LSRK = MODE == kModeLsrk;
+  constexpr bool GRADM = MODE == kModeGrad || MODE == kModeGradFace;
   static_assert(VOL == kVolCuda || (std::is_same<Real, float>::value && (MODE == kModeRhs || MODE == kModeLsrk)),
                 "the tensor-core volume form belongs to the FP32 forward path");
   const Real sgnA = MODE == kModeAdj ? Real(-1) : Real(1);
@@ -484,7 +487,9 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
   // accumulated term by term from the state and metric tiles (no staging, no
   // barrier between directions).  Staged form: the left-hand side, with
   // A_+(m_b) u_b staged per direction.
-  if constexpr (VOL != kVolCuda) {
+  if constexpr (MODE == kModeGradFace) {
+    // no volume term: the operator output comes from the forward stage
+  } else if constexpr (VOL != kVolCuda) {
     // Tensor-core form: per direction, write u and F = A_+(Ja^i) u line-major,
     // contract all lines by D on the tensor cores, then acc += D F + A_+(Ja^i_a) D u.
     using T = TcShape<N>;
@@ -697,7 +702,7 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
         // 1/2 (A(m) - tau S(m)) du (1/J)/w_0 = -1/2 (A_+ du + tau S du) (1/J)/w_0
 #pragma unroll
         for (int q = 0; q < 9; ++q) flux[q] = s * (sgnA * Ad[q] + tau * Sd[q]);
-        if constexpr (MODE == kModeGrad) {
+        if constexpr (GRADM) {
           // d(flux)/dZs and d(flux)/dZp against Q_e^{-1} w at this node.
           const size_t gi = static_cast<size_t>(ei) * Np + vn;
           const Real* matg = static_cast<const Real*>(p.mat);
@@ -741,8 +746,10 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
 #pragma unroll
         for (int q = 0; q < 9; ++q) flux[q] = s * sgnA * Ad[q];
       }
+      if constexpr (MODE != kModeGradFace) {
 #pragma unroll
-      for (int q = 0; q < 9; ++q) x_s[q * NFI + it] = flux[q];
+        for (int q = 0; q < 9; ++q) x_s[q * NFI + it] = flux[q];
+      }
     }
   }
   __syncthreads();
@@ -761,12 +768,18 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
 #pragma unroll
       for (int q = 0; q < 9; ++q) r[q] += x_s[q * NFI + fb0 + f * nf + pidx];
     };
-    if (ix == 0) add_face(0, iy + n * iz);
-    if (ix == N) add_face(1, iy + n * iz);
-    if (iy == 0) add_face(2, ix + n * iz);
-    if (iy == N) add_face(3, ix + n * iz);
-    if (iz == 0) add_face(4, ix + n * iy);
-    if (iz == N) add_face(5, ix + n * iy);
+    if constexpr (MODE == kModeGradFace) {
+      // dt (K u + f) of this node from the forward stage (below)
+#pragma unroll
+      for (int q = 0; q < 9; ++q) r[q] = p.rout[q * fstride + gidx];
+    } else {
+      if (ix == 0) add_face(0, iy + n * iz);
+      if (ix == N) add_face(1, iy + n * iz);
+      if (iy == 0) add_face(2, ix + n * iz);
+      if (iy == N) add_face(3, ix + n * iz);
+      if (iz == 0) add_face(4, ix + n * iy);
+      if (iz == N) add_face(5, ix + n * iy);
+    }
 
     if constexpr (MODE == kModeAdj) {
       // lu <- lu + dt (w J) r : M Q L_rev z without Q^{-1} (Q^{-1} and Q cancel)
@@ -774,18 +787,19 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
 #pragma unroll
       for (int q = 0; q < 9; ++q) p.out[q * fstride + gidx] = p.res[q * fstride + gidx] + p.dt * wj * r[q];
     }
-    if constexpr (MODE == kModeGrad) {
-      // dt w^T (d Q^{-1}/dm) (K u + f) at this node, f the point force (before Q^{-1})
+    if constexpr (GRADM) {
+      // dt w^T (d Q^{-1}/dm) (K u + f) at this node, f the point force (before Q^{-1});
+      // GRAD_FACE reads dt (K u + f) as the forward stage produced it
       const Real* matg = static_cast<const Real*>(p.mat);
       const Real irho = matg[e];
-      if (e == p.src_elem) {
+      if (MODE == kModeGrad && e == p.src_elem) {
 #pragma unroll
         for (int q = 0; q < 3; ++q) r[q] += static_cast<Real>(p.src_amp * p.src_w[q * Np + node]) / irho;
       }
       Real w[9];
 #pragma unroll
       for (int q = 0; q < 9; ++q) w[q] = p.res[q * fstride + gidx];
-      const Real dtg = static_cast<Real>(p.dt);
+      const Real dtg = MODE == kModeGrad ? static_cast<Real>(p.dt) : Real(1);
       gnode[0] = -dtg * irho * irho * (w[0] * r[0] + w[1] * r[1] + w[2] * r[2]);
       gnode[1] = dtg * (w[3] + w[4] + w[5]) * (r[3] + r[4] + r[5]);
       gnode[2] = dtg * (2 * (w[3] * r[3] + w[4] * r[4] + w[5] * r[5]) + w[6] * r[6] + w[7] * r[7] + w[8] * r[8]);
@@ -797,6 +811,17 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
     const Real irho = mat[e];
     const Real lam = mat[p.nel + e];
     const Real mu = mat[2 * p.nel + e];
+    if constexpr (LSRK && std::is_same<Real, double>::value) {
+      if (p.rout != nullptr) {
+        // dt (K u + f) before Q^{-1}, kept for the adjoint's gradient terms
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+          double v = r[q];
+          if (q < 3 && e == p.src_elem) v += p.dt * p.src_amp * p.src_w[q * Np + node] / irho;
+          p.rout[q * fstride + gidx] = v;
+        }
+      }
+    }
     Real rr[9];
     rr[0] = irho * r[0];
     rr[1] = irho * r[1];
@@ -855,7 +880,7 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
     }
     }
   }
-  if constexpr (MODE == kModeGrad) {
+  if constexpr (GRADM) {
     // Sum the node terms of each element in a fixed order (the state tile is free now).
     __syncthreads();
     if (in_tile) {
@@ -1105,22 +1130,22 @@ cudaError_t launch_stage_any(int N, bool lsrk, const StageParams& p, cudaStream_
 #undef DGW_CASE
 }
 
-// One adjoint stage in one launch: every CTA takes its tile in GRAD mode (the
-// forward operator on the stage input, gradient terms against the weight w),
+// One adjoint stage in one launch: every CTA takes its tile in GRAD (or
+// GRAD_FACE) mode (the gradient terms of the stage input against the weight w),
 // then in ADJ mode (the reversed operator on z, added to lu).  The two modes
 // read the same metric terms, neighbour map, face impedances and medium of the
 // tile, which the second pass finds in cache; they write disjoint outputs.
-template <int N>
+template <int N, int GMODE>
 __global__ void __launch_bounds__(Shape<N>::NT) stage_adjgrad_kernel(const StageParams g, const StageParams a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* D_s = reinterpret_cast<double*>(smem_raw + StageSmem<N, double>::d_off);
   for (int i = threadIdx.x; i < Shape<N>::n * Shape<N>::n; i += Shape<N>::NT) D_s[i] = g.D[i];
-  stage_tile<N, double, kModeGrad>(g, blockIdx.x, smem_raw);
+  stage_tile<N, double, GMODE>(g, blockIdx.x, smem_raw);
   __syncthreads();
   stage_tile<N, double, kModeAdj>(a, blockIdx.x, smem_raw);
 }
 
-template <int N>
+template <int N, int GMODE>
 cudaError_t launch_stage_adjgrad_t(const StageParams& g, const StageParams& a, cudaStream_t s) {
   const size_t smem = StageSmem<N, double>::bytes;
   static std::atomic<unsigned long long> ready{0};
@@ -1129,7 +1154,7 @@ cudaError_t launch_stage_adjgrad_t(const StageParams& g, const StageParams& a, c
   if (err != cudaSuccess) return err;
   const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
   if (!(ready.load(std::memory_order_relaxed) & bit)) {
-    err = cudaFuncSetAttribute(stage_adjgrad_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    err = cudaFuncSetAttribute(stage_adjgrad_kernel<N, GMODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     ready.fetch_or(bit, std::memory_order_relaxed);
   }
@@ -1138,15 +1163,16 @@ cudaError_t launch_stage_adjgrad_t(const StageParams& g, const StageParams& a, c
   StageParams gq = g, aq = a;
   finish_stage_params(gq);
   finish_stage_params(aq);
-  stage_adjgrad_kernel<N><<<(unsigned)blocks, Shape<N>::NT, smem, s>>>(gq, aq);
+  stage_adjgrad_kernel<N, GMODE><<<(unsigned)blocks, Shape<N>::NT, smem, s>>>(gq, aq);
   return cudaGetLastError();
 }
 
+// g.rout set: the gradient terms take the operator output from it (GRAD_FACE).
 inline cudaError_t launch_stage_adjgrad_any(int N, const StageParams& g, const StageParams& a, cudaStream_t s) {
   switch (N) {
-#define DGW_GCASE(NN) \
-  case NN:            \
-    return launch_stage_adjgrad_t<NN>(g, a, s);
+#define DGW_GCASE(NN)                                                                                      \
+  case NN:                                                                                                 \
+    return g.rout ? launch_stage_adjgrad_t<NN, kModeGradFace>(g, a, s) : launch_stage_adjgrad_t<NN, kModeGrad>(g, a, s);
     DGW_GCASE(1) DGW_GCASE(2) DGW_GCASE(3) DGW_GCASE(4) DGW_GCASE(5) DGW_GCASE(6) DGW_GCASE(7)
 #undef DGW_GCASE
     default:

@@ -22,7 +22,7 @@ struct StateHeader {
   int64_t nel;
   int64_t step;
   double t;
-  uint64_t mesh_fingerprint;   // FNV-1a over degree, system, connectivity, boundary tags, h_min, c_max
+  uint64_t mesh_fingerprint;   // FNV-1a over degree, system, connectivity, boundary tags, h_min, c_max, medium
   uint64_t payload_hash;       // FNV-1a over the payload's 64-bit words
   uint64_t payload_bytes;
   uint64_t reserved;
@@ -63,6 +63,7 @@ uint64_t mesh_fingerprint(const dgw_ctx* c) {
   h = fnv_bytes(h, c->bc.data(), c->bc.size());
   h = fnv_bytes(h, &c->h_min, sizeof c->h_min);
   h = fnv_bytes(h, &c->c_max, sizeof c->c_max);
+  h = fnv_bytes(h, &c->medium_hash, sizeof c->medium_hash);
   return h;
 }
 

@@ -282,3 +282,32 @@ def test_gradient_central_differences_at_recipe_size():
         assert err <= 1e-6, (e, p, g[p, e], fd)
     print(f"adjoint recipe 32^3 N=4 500 steps: misfit {float(J.detach()):.3e}, worst FD relative error {worst:.2e}")
     s.close()
+
+
+def test_low_memory_adjoint_gives_the_same_gradient():
+    """The adjoint keeps every stage's operator output for the gradient terms
+    (default) or, with DGW_ADJOINT_LOW_MEMORY=1, recomputes it (the path taken
+    when the larger scratch does not fit): the same lam_u and register, and the
+    same gradient to rounding (the operator output is scaled by dt at another
+    point of the arithmetic)."""
+    import os
+    import torch
+    s, op, mesh, _ = problem(E=3, N=3, seed=35)
+    rng = np.random.default_rng(6)
+    shape = (9, mesh.nel, 64)
+    u0 = torch.from_numpy(1e-2 * rng.standard_normal(shape)).cuda()
+    g = torch.from_numpy(rng.standard_normal((4, 2, 3))).cuda()
+    lu0 = rng.standard_normal(shape)
+    out = []
+    for low in ("0", "1"):
+        os.environ["DGW_ADJOINT_LOW_MEMORY"] = low
+        try:
+            lu = torch.from_numpy(lu0).cuda()
+            lr = torch.zeros_like(lu)
+            grad = torch.zeros((3, mesh.nel), dtype=torch.float64, device="cuda")
+            s.adjoint_traces(lu, lr, grad, u0, g, 0.01, 4, t0=0.02)
+            out.append((lu.cpu().numpy(), lr.cpu().numpy(), grad.cpu().numpy()))
+        finally:
+            del os.environ["DGW_ADJOINT_LOW_MEMORY"]
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    assert rel_l2(out[0][2], out[1][2]) < 1e-13
