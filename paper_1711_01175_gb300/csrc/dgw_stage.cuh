@@ -170,6 +170,11 @@ __device__ __forceinline__ void prefetch_l2(const void* lo, const void* hi) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(a), "r"((unsigned)(b - a)) : "memory");
 }
 
+// Hint: bring the line holding a into L1.
+__device__ __forceinline__ void prefetch_l1(const void* a) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(a));
+}
+
 // Volume-term form.  Combined: per direction and line node b, A_+(D_ab (m_a + m_b)) u_b
 // (24 operations).  Staged: A_+(m) u of the tile staged in shared memory, then
 // the two contractions and A_+(m_a) applied to D u (36 + 18 n operations per
@@ -211,6 +216,33 @@ struct TcShape {
 
 __device__ __forceinline__ int tc_swz(int block) { return ((block & 1) << 1) | ((block >> 1) & 1); }
 
+// Preferred shared-memory carveout of a stage kernel, in percent of the
+// largest (100: the most shared memory, the least L1).  The FP32 CUDA-core
+// kernels read the neighbour traces and re-read the FP64 state in the epilogue
+// through L1, and gain from a larger L1 even at a resident CTA fewer.  Measured
+// on GB300, mixed stage in ms at 100 % / 72 % / 58 % (72 %: 164 KB of shared
+// memory, 58 %: 132 KB): N = 1 3.92 / 4.33 / 6.90, N = 2 3.48 / 3.94 / 4.82,
+// N = 3 3.14 / 3.10 / 3.54, N = 4 2.99 / 2.70 / 2.83, N = 5 2.85 / 2.73 / 2.73,
+// N = 6 3.16 / 3.00 / 2.99, N = 7 3.36 / 3.31 / 4.10.  FP64 kernels (bound by
+// their FP64 pipe) do not change and keep the largest shared memory.
+template <int N, typename Real, int VOL>
+__host__ __device__ constexpr int stage_carveout() {
+  if constexpr (std::is_same<Real, float>::value && VOL == kVolCuda) {
+    return N <= 2 ? 100 : ((N == 5 || N == 6) ? 58 : 72);
+  } else {
+    return 100;
+  }
+}
+
+// L1 prefetch of the RK register (read in the epilogue) and of the face items'
+// neighbour traces (read in the face phase), issued with the tile load.  Measured
+// on GB300, mixed stage: N = 7 +7 % (40^3: 3.31 -> 3.09 ms, 48^3: 5.72 -> 5.34 ms);
+// N = 3, 4, 5, 6 0.3 to 4.6 % slower.  Used for the FP32 CUDA-core kernel at N = 7.
+template <int N, typename Real, int VOL>
+__host__ __device__ constexpr bool l1_prefetch() {
+  return std::is_same<Real, float>::value && VOL == kVolCuda && N == 7;
+}
+
 template <int N, typename Real, int VOL = kVolCuda>
 struct StageSmem {
   using S = Shape<N>;
@@ -227,8 +259,8 @@ struct StageSmem {
   static constexpr size_t fbytes = sizeof(Real) * fwords;
   static constexpr size_t g_off = f_off + ((fbytes + 15) / 16) * 16;     // Real [NTILE][PK] Ja, 1/J
   static constexpr size_t d_off = g_off + sizeof(Real) * S::NTILE * PK;  // Real [n*n]
-  static constexpr size_t e_off = ((d_off + sizeof(Real) * S::n * S::n + 15) / 16) * 16;  // double [32] reduction
-  static constexpr size_t bytes = e_off + sizeof(double) * 32;
+  static constexpr size_t e_off = ((d_off + sizeof(Real) * S::n * S::n + 15) / 16) * 16;  // double [NT/32] reduction
+  static constexpr size_t bytes = e_off + sizeof(double) * (S::NT / 32);
 };
 
 // Slots of the metric terms in a node's geometry tile: Ja^dir_k and 1/J.  FP32
@@ -431,6 +463,18 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
     }
   }
 
+  if constexpr (l1_prefetch<N, Real, VOL>()) {
+    // neighbour traces of this thread's face items into L1
+    for (int it = t; it < NFI; it += NT) {
+      const int eli = it / (6 * nf);
+      if (e0 + eli >= p.nel) break;
+      const int g = p.vmapP[static_cast<size_t>(e0 + eli) * 6 * nf + (it - eli * 6 * nf)];
+      if (g >= 0 && static_cast<long long>(g) < p.nel * Np) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) prefetch_l1(p.u_in + q * fstride + g);
+      }
+    }
+  }
   Real uw[9];      // this node's state (kept for the tensor-core volume form)
   if (in_tile) {
     Real w[10], gj[10];
@@ -439,6 +483,12 @@ __device__ __forceinline__ void stage_tile(const StageParams& p, long long tile,
       for (int q = 0; q < 9; ++q) w[q] = to_real<Real>(p.u_in[q * fstride + gidx]);
 #pragma unroll
       for (int c = 0; c < 10; ++c) gj[c] = geo[c * fstride + gidx];
+      if constexpr (LSRK && l1_prefetch<N, Real, VOL>()) {
+        if (!first) {
+#pragma unroll
+          for (int q = 0; q < 9; ++q) prefetch_l1(p.res + q * fstride + gidx);
+        }
+      }
       if constexpr (kDebugChecks) {
         bool finite = true;
 #pragma unroll
@@ -1055,7 +1105,7 @@ cudaError_t prepare_stage_batch_t() {
   cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                              (int)cudaSharedmemCarveoutMaxShared);
+                              stage_carveout<N, Real, kVolCuda>());
 }
 
 template <typename Real>
@@ -1099,7 +1149,7 @@ cudaError_t launch_stage_t(const StageParams& p, cudaStream_t s) {
     err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     err = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                               (int)cudaSharedmemCarveoutMaxShared);
+                               stage_carveout<N, Real, VOL>());
     if (err != cudaSuccess) return err;
     ready.fetch_or(bit, std::memory_order_relaxed);
   }
