@@ -494,7 +494,8 @@ def _cpu_model():
         with open("/proc/cpuinfo") as f:
             for line in f:
                 if line.lower().startswith(("model name", "cpu part", "hardware")):
-                    return line.split(":", 1)[1].strip()
+                    key, val = line.split(":", 1)
+                    return val.strip() if key.lower().startswith("model") else f"{key.strip()} {val.strip()}"
     except OSError:
         pass
     import platform

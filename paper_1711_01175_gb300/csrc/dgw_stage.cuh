@@ -1052,6 +1052,8 @@ __device__ __forceinline__ void stage_batch_body(const BatchLaunch& L, const Bat
   ps.pf_elems = L.pf_elems;
   ps.grad_el = nullptr;
   ps.grad_face = nullptr;
+  ps.rout = nullptr;        // no adjoint output in batches
+  ps.fault = nullptr;       // batches record no debug faults
   ps.src_elem = b.src_elem;
   ps.src_w = b.src_w;
   ps.dt_f = b.dt_f;
