@@ -223,12 +223,16 @@ __device__ __forceinline__ int tc_swz(int block) { return ((block & 1) << 1) | (
 // on GB300, mixed stage in ms at 100 % / 72 % / 58 % (72 %: 164 KB of shared
 // memory, 58 %: 132 KB): N = 1 3.92 / 4.33 / 6.90, N = 2 3.48 / 3.94 / 4.82,
 // N = 3 3.14 / 3.10 / 3.54, N = 4 2.99 / 2.70 / 2.83, N = 5 2.85 / 2.73 / 2.73,
-// N = 6 3.16 / 3.00 / 2.99, N = 7 3.36 / 3.31 / 4.10.  FP64 kernels (bound by
-// their FP64 pipe) do not change and keep the largest shared memory.
+// N = 6 3.16 / 3.00 / 2.99, N = 7 3.36 / 3.31 / 4.10.  The tensor-core forms
+// (BF16, 100 % / 86 % / 72 %): N = 4 4.83 / 4.82 / 4.76, N = 7 (48^3) 6.05 /
+// 6.05 / 5.81 ms; other degrees not measured.  FP64 kernels (bound by their
+// FP64 pipe) do not change and keep the largest shared memory.
 template <int N, typename Real, int VOL>
 __host__ __device__ constexpr int stage_carveout() {
   if constexpr (std::is_same<Real, float>::value && VOL == kVolCuda) {
     return N <= 2 ? 100 : ((N == 5 || N == 6) ? 58 : 72);
+  } else if constexpr (std::is_same<Real, float>::value) {
+    return (N == 4 || N == 7) ? 72 : 100;
   } else {
     return 100;
   }
