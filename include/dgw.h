@@ -254,7 +254,13 @@ dgw_status dgw_receivers_adjoint(dgw_ctx* ctx, double* lam_u, const double* g, v
 /* dt = cfl * h / (c_max * N^2) with h the smallest element edge length
  * (distance between adjacent element corner nodes) and c_max the largest
  * P-wave speed sqrt((lam + 2 mu) / rho); the CFL convention of the paper's
- * time-dependent transport experiments (Section 6.1). */
+ * time-dependent transport experiments (Section 6.1).  The N^2 scaling
+ * understates the stiffness of the elastic operator at low degree: with the
+ * upwind flux and LSRK(5,4), a rough state (random nodal values, warped and
+ * rotated elements, heterogeneous medium) grows without bound at CFL 0.5 for
+ * N = 1 and 2; the stable limits measured there are about 0.125-0.15 (N = 1)
+ * and 0.45-0.5 (N = 2), while N = 3 to 7 are stable at 0.5.  Set cfg.cfl
+ * accordingly for N <= 2. */
 dgw_status dgw_dt_cfl(dgw_ctx* ctx, double* dt_out);
 
 /* ---- Batches: many solves advanced together (serving) -------------------

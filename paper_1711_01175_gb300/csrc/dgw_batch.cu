@@ -151,7 +151,7 @@ dgw_status dgw_batch_create(dgw_batch** out, int device, int N, int precision, i
   L.tau_f = static_cast<float>(L.tau);
   L.hlift_f = static_cast<float>(0.5 * L.w_end_inv);
   for (int i = 0; i < (N + 1) * (N + 1); ++i) L.D[i] = R.D[i];
-  L.pf_elems = 1LL * b->sm_count * epb;
+  L.pf_elems = 1LL * b->sm_count * epb * dgw::stage_pf_tenths(N, b->precision) / 10;
   cudaStream_t cs = b->capture;
   e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return bail(DGW_ERR_CUDA, std::string("begin capture: ") + cudaGetErrorString(e));

@@ -106,19 +106,7 @@ dgw_status launch_stage(dgw_ctx* c, const double* u_in, double* out, double* res
   {
     int epb = 0, nthreads = 0;
     dgw::stage_shape(c->cfg.N, &epb, &nthreads);
-    // L2 prefetch distance in tenths of one CTA per SM ahead.  FP64: one CTA per SM
-    // (its stage is bound by the FP64 pipe; 0.5 and 1 time alike at N = 4 and 7).
-    // FP32 CUDA-core stage: the fastest of 0 (off), 0.1, 0.2, 0.3, 0.5 and 1 at each
-    // degree on 64^3 (N <= 4), 56^3 (N = 5, 6) and 48^3 (N = 7); at N = 7 the L1
-    // prefetch of the neighbour traces already covers the gather and the L2
-    // prefetch evicts neighbour traces before they are gathered.  Tensor-core
-    // forms (no L1 prefetch): 0.2 at N = 7 (the fastest of 0, 0.2, 0.5 and 1 on
-    // 48^3), one CTA per SM elsewhere (0.2 to 1 time alike at N = 4).
-    static const int kMixedPfTenths[8] = {10, 2, 2, 1, 10, 2, 1, 0};
-    const int tenths = c->cfg.precision == DGW_PRECISION_MIXED ? kMixedPfTenths[c->cfg.N]
-                       : (c->cfg.precision != DGW_PRECISION_FP64 && c->cfg.N == 7) ? 2
-                                                                                  : 10;
-    p.pf_elems = 1LL * c->sm_count * epb * tenths / 10;
+    p.pf_elems = 1LL * c->sm_count * epb * dgw::stage_pf_tenths(c->cfg.N, c->cfg.precision) / 10;
   }
   p.src_elem = c->src_elem;
   p.src_w = c->src_w;

@@ -165,6 +165,21 @@ cudaError_t launch_stage_mixed(int N, bool lsrk, const StageParams& p, cudaStrea
 cudaError_t launch_stage_mixed_tc(int N, int fmt, bool lsrk, const StageParams& p, cudaStream_t s);
 // Precisions whose geometry, face and material arrays are FP32.
 inline bool fp32_arrays(int precision) { return precision != DGW_PRECISION_FP64; }
+// L2 bulk prefetch distance of the stage kernels, in tenths of one CTA per SM
+// ahead (StageParams::pf_elems = SMs x elements per CTA x tenths / 10).
+// FP64: one CTA per SM (its stage is bound by the FP64 pipe; 0.5 and 1 time alike
+// at N = 4 and 7).  FP32 CUDA-core stage: the fastest of 0 (off), 0.1, 0.2, 0.3,
+// 0.5 and 1 at each degree on 64^3 (N <= 4), 56^3 (N = 5, 6) and 48^3 (N = 7);
+// at N = 3, 5, 6 and 7 the kernel's L1 prefetch of the neighbour traces covers
+// the gather and an L2 prefetch ahead only evicts traces before they are
+// gathered.  Tensor-core forms (no L1 prefetch): 0.2 at N = 7 (the fastest of 0,
+// 0.2, 0.5 and 1 on 48^3), one CTA per SM elsewhere (0.2 to 1 alike at N = 4).
+inline int stage_pf_tenths(int N, int precision) {
+  static const int kMixed[8] = {10, 2, 2, 0, 10, 0, 0, 0};
+  if (precision == DGW_PRECISION_MIXED) return kMixed[N];
+  if (precision != DGW_PRECISION_FP64 && N == 7) return 2;
+  return 10;
+}
 cudaError_t launch_stage_adjoint(int N, int mode, const StageParams& p, cudaStream_t s);   // mode 2: ADJ, 3: GRAD
 // GRAD (params g) then ADJ (params a) on every tile, in one launch.
 cudaError_t launch_stage_adjgrad(int N, const StageParams& g, const StageParams& a, cudaStream_t s);

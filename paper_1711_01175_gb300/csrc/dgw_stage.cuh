@@ -240,11 +240,13 @@ __host__ __device__ constexpr int stage_carveout() {
 
 // L1 prefetch of the RK register (read in the epilogue) and of the face items'
 // neighbour traces (read in the face phase), issued with the tile load.  Measured
-// on GB300, mixed stage: N = 7 +7 % (40^3: 3.31 -> 3.09 ms, 48^3: 5.72 -> 5.34 ms);
-// N = 3, 4, 5, 6 0.3 to 4.6 % slower.  Used for the FP32 CUDA-core kernel at N = 7.
+// on GB300, mixed stage, with the L2 bulk prefetch off at the same degrees (the
+// two compete for L2: an L2 prefetch ahead evicts traces before their gather):
+// N = 3 +1.5 %, 5 +1.7 %, 6 +0.9 %, 7 +6 % over the best L2 prefetch distance
+// alone; N = 4 1 % slower.  Used for the FP32 CUDA-core kernel at N = 3, 5, 6, 7.
 template <int N, typename Real, int VOL>
 __host__ __device__ constexpr bool l1_prefetch() {
-  return std::is_same<Real, float>::value && VOL == kVolCuda && N == 7;
+  return std::is_same<Real, float>::value && VOL == kVolCuda && (N == 3 || N >= 5);
 }
 
 template <int N, typename Real, int VOL = kVolCuda>

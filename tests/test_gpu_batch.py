@@ -76,16 +76,18 @@ def alone(item, nsteps, t0=0.0):
     return u.cpu().numpy()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_batch_matches_single_solves_with_composition_change(precision):
+@pytest.mark.parametrize("precision,N", [("fp64", 4), ("mixed", 4), ("mixed", 5)])
+def test_batch_matches_single_solves_with_composition_change(precision, N):
+    """N = 5 reaches the FP32 stage's L1-prefetch form (N = 3, 5, 6, 7), N = 4 the
+    form without it."""
     import torch
     stream = torch.cuda.current_stream().cuda_stream
-    items = [make_solve(2, 4, 1, precision), make_solve(3, 4, 2, precision), make_solve(2, 4, 3, precision, False)]
-    late = make_solve(3, 4, 4, precision)
+    items = [make_solve(2, N, 1, precision), make_solve(3, N, 2, precision), make_solve(2, N, 3, precision, False)]
+    late = make_solve(3, N, 4, precision)
     for it in items + [late]:
         it["u"] = torch.from_numpy(it["u0"]).cuda()
         it["res"] = torch.zeros_like(it["u"])
-    b = Batch(4, precision)
+    b = Batch(N, precision)
     # pairs 0-1: first three solves; then solve 1 leaves and `late` joins for 2 more pairs
     b.set(items, [0.0, 0.0, 0.0], stream)
     b.run(2, stream)
