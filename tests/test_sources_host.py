@@ -28,3 +28,24 @@ def test_batch_body_sets_every_stage_parameter_the_tile_reads():
     read = set(re.findall(r"\bp\.(\w+)", tile)) & fields
     assert read, "no stage parameters found"
     assert not (read - assigned), sorted(read - assigned)
+
+
+def test_l2_prefetch_is_off_exactly_where_the_l1_prefetch_runs():
+    """The FP32 CUDA-core stage either prefetches the neighbour traces into L1
+    (l1_prefetch) or prefetches later tiles into L2 (stage_pf_tenths): an L2
+    prefetch ahead evicts the traces the L1 form is about to gather, so the two
+    are chosen per degree as a pair.  The mixed table must be zero at exactly
+    the degrees the L1 form is compiled for."""
+    stage = _read("dgw_stage.cuh")
+    head = _read("dgw_internal.cuh")
+    m = re.search(r"constexpr bool l1_prefetch\(\) \{\s*return std::is_same<Real, float>::value && "
+                  r"VOL == kVolCuda && \(([^;]*)\);", stage)
+    assert m, "l1_prefetch condition not found"
+    cond = m.group(1).replace("||", " or ").replace("&&", " and ")
+    l1 = {N for N in range(1, 8) if eval(cond, {"__builtins__": {}, "N": N})}
+    t = re.search(r"static const int kMixed\[8\] = \{([^}]*)\};", head)
+    assert t, "mixed prefetch table not found"
+    tenths = [int(v) for v in t.group(1).split(",")]
+    assert len(tenths) == 8
+    assert {N for N in range(1, 8) if tenths[N] == 0} == l1
+    assert l1 == {3, 5, 6, 7}
